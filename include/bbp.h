@@ -1,0 +1,145 @@
+/*
+ * bbp.h -- C ABI of libbbp: BBP digit extraction of pi on one NVIDIA GB300 (sm_103a).
+ *
+ * The library evaluates Bellard's BBP-type series (Eq. 2 of Sze, "The Two
+ * Quadrillionth Bit of pi is 0!", arXiv:1008.3171) -- or the original BBP series
+ * (Eq. 1) -- to extract P bits of pi starting at binary position n, as exact
+ * integer work on the GPU.  Sec. 3 (Eq. 3-5) defines the computation:
+ *
+ *   d = n - 1; {2^d pi} = { sum_j sign_j { sum_k (-1)^(alt k) 2^(d + c_j - step k) / (a_j k + b_j) } }
+ *
+ *   head terms (exponent e >= 0):  t = floor((2^e mod m) 2^W / m)
+ *   tail terms (e < 0):            t = floor(2^(W+e) / m), up to the first zero
+ *
+ * summed as W-bit two's-complement fixed point (mod 2^W), W = roundup(P,32) + G.
+ *
+ * Conventions for every function below:
+ *   - Bit positions count from 1 after the radix point (Sec. 2 footnote: the eight
+ *     bits from position 9 are 0x3F).  n = 0 is invalid.
+ *   - Limb arrays are little-endian uint32 (limb 0 least significant), W/32 limbs.
+ *   - Output bit strings are MSB-first bytes: out[0] bit 7 is bit n; the unused low
+ *     bits of the last byte are 0.
+ *   - Every function returns a bbp_status; no C++ exception crosses the ABI.
+ *   - A plan is not thread-safe: one host thread at a time per plan.
+ *   - Buffers named h_* or without prefix are host memory owned by the caller;
+ *     d_* are device memory on the plan's device owned by the caller.
+ *   - Moduli must stay below 2^60: n up to about 1.1e18 (BBP_ERANGE beyond).
+ */
+#ifndef BBP_H
+#define BBP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BBP_ABI_VERSION 1u
+
+typedef enum bbp_status {
+  BBP_OK = 0,
+  BBP_PENDING = 1,           /* bbp_poll: the query has not finished yet */
+  BBP_EINVAL = -1,           /* bad argument (n = 0, P = 0, denominator out of range, ...) */
+  BBP_ENOMEM = -2,           /* host or device allocation failed */
+  BBP_ECUDA = -3,            /* a CUDA call failed; the plan should be destroyed */
+  BBP_EBUSY = -4,            /* bbp_submit: no accumulator slot or memory free right now */
+  BBP_ETIMEOUT = -5,         /* a bounded device-side wait gave up */
+  BBP_ERANGE = -6,           /* n so large that a modulus would reach 2^60 */
+  BBP_EINVALID_BITS = -7,    /* strict mode: fewer than P bits certified */
+  BBP_ENOTFOUND = -8         /* unknown ticket */
+} bbp_status;
+
+/* Eq. 2 (Bellard, 7 series, step 10, alternating) or Eq. 1 (BBP, 4 series, step 4). */
+typedef enum bbp_formula { BBP_BELLARD = 0, BBP_BBP = 1 } bbp_formula;
+
+typedef struct bbp_plan_s* bbp_plan;
+
+typedef struct bbp_plan_opts {
+  int device;               /* CUDA device ordinal */
+  void* stream;             /* cudaStream_t for all work; NULL: the plan creates its own */
+  uint32_t guard_bits;      /* G: positive multiple of 32; 0 selects 64 */
+  size_t accum_mem_budget;  /* bytes of device accumulator memory for queued queries; 0: 64 MiB */
+  uint32_t max_slots;       /* concurrent queries admitted by bbp_submit; 0: 4096 */
+  const char* tune_table;   /* path of an autotune table (JSON) or NULL for built-in defaults */
+  uint32_t profile;         /* 1: time head-kernel launches with CUDA events (see bbp_stats) */
+  uint32_t strict;          /* 1: bbp_bits fails with BBP_EINVALID_BITS unless all P bits certify */
+} bbp_plan_opts;
+
+/* Counters of the most recent compute call on a plan. */
+typedef struct bbp_stats {
+  uint64_t terms;           /* terms evaluated (head + tail) */
+  uint64_t head_terms;      /* head terms (modular exponentiations) */
+  uint64_t head_launches;   /* head-kernel launches */
+  uint64_t kernel_launches; /* all kernel launches */
+  double imad_model;        /* 32-bit integer multiply instructions the head terms need (model) */
+  double head_ms;           /* device time of the head launches (profile = 1), else 0 */
+} bbp_stats;
+
+/* ABI version of the loaded library; equals BBP_ABI_VERSION when headers match. */
+uint32_t bbp_abi_version(void);
+
+/* Static English text for a status code; never NULL. */
+const char* bbp_status_str(bbp_status s);
+
+/* Fills *opts with defaults (device 0, own stream, G = 64, no profiling). */
+void bbp_plan_opts_default(bbp_plan_opts* opts);
+
+/* Creates a plan on opts->device (NULL opts: defaults).  The plan owns its device
+ * buffers and, if opts->stream is NULL, its stream.  Release with bbp_plan_destroy. */
+bbp_status bbp_plan_create(bbp_plan* out, const bbp_plan_opts* opts);
+
+/* Waits for the plan's stream, then frees everything the plan owns.  NULL is accepted. */
+bbp_status bbp_plan_destroy(bbp_plan p);
+
+/* W = roundup(P, 32) + G for the plan's guard bits G (host-only, no GPU work). */
+uint32_t bbp_working_bits(bbp_plan p, uint32_t P);
+
+/* Host-only extent of one series (Eq. 4): *head_end = first k with exponent < 0,
+ * *natural_end = first tail k whose truncated term floor(2^(W+e)/m) is 0.
+ * Needs no GPU.  EINVAL for n = 0, bad formula/denominator or W not a multiple of 32. */
+bbp_status bbp_series_extent(bbp_formula f, uint32_t denominator, uint64_t n, uint32_t W,
+                             uint64_t* head_end, uint64_t* natural_end);
+
+/* Eq. 3-5, one series over one k-range:
+ *   out_limbs = sign_j * sum_{k in [k_begin, min(k_end, natural_end))} (-1)^(alt k) t_{j,k}  (mod 2^W)
+ * with W = bbp_working_bits(p, P).  k_end = UINT64_MAX means the natural end.
+ * out_limbs: caller-owned host array of W/32 uint32.  Blocks until done.
+ * EINVAL: n = 0, P = 0, denominator >= series count, k_begin > k_end. */
+bbp_status bbp_partial_sum(bbp_plan p, bbp_formula f, uint32_t denominator, uint64_t k_begin,
+                           uint64_t k_end, uint64_t n, uint32_t P, uint32_t* out_limbs);
+
+/* As bbp_partial_sum, but writes W/32 limbs to device memory d_out_limbs and
+ * returns once the work is queued on `stream` (NULL: the plan's stream). */
+bbp_status bbp_partial_sum_async(bbp_plan p, bbp_formula f, uint32_t denominator, uint64_t k_begin,
+                                 uint64_t k_end, uint64_t n, uint32_t P, uint32_t* d_out_limbs,
+                                 void* stream);
+
+/* Bits n .. n+P-1 of pi by Eq. 2.  out: caller-owned ceil(P/8) host bytes, MSB first.
+ * valid_bits (may be NULL): how many leading bits the guard-bit error bound certifies
+ * (|S - exact| < N + J + 1 units for N evaluated terms and J series).  Blocks. */
+bbp_status bbp_bits(bbp_plan p, uint64_t n, uint32_t P, uint8_t* out, uint32_t* valid_bits);
+
+/* bbp_bits with a choice of formula (Eq. 1 or Eq. 2). */
+bbp_status bbp_bits_formula(bbp_plan p, bbp_formula f, uint64_t n, uint32_t P, uint8_t* out,
+                            uint32_t* valid_bits);
+
+/* Device-pointer form: d_out (ceil(P/8) bytes), d_valid (one uint32, may be NULL)
+ * and d_limbs (W/32 uint32 of the raw sum, may be NULL) are caller-owned device
+ * memory; returns once queued on `stream` (NULL: the plan's stream). */
+bbp_status bbp_bits_async(bbp_plan p, bbp_formula f, uint64_t n, uint32_t P, uint8_t* d_out,
+                          uint32_t* d_valid, uint32_t* d_limbs, void* stream);
+
+/* Counters of the last compute call on this plan. */
+bbp_status bbp_plan_stats(bbp_plan p, bbp_stats* out);
+
+/* Issue-rate probe of the integer pipes (kind 0: 32-bit multiply-add low half,
+ * 1: high half, 2: 32x32->64 wide, 3: 32-bit add).  Runs one CTA of 1024 threads
+ * per SM and reports warp-lane operations per SM clock (median over SMs). */
+bbp_status bbp_imad_probe(bbp_plan p, int kind, double* lanes_per_clk_per_sm);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BBP_H */

@@ -1,0 +1,256 @@
+"""Python binding of libbbp: BBP digit extraction of pi on one GB300 (sm_103a).
+
+Argument marshalling only.  Every step of the computation runs in the CUDA
+kernels of ``libbbp.so`` (built in-tree by ``build()``); there is no CPU
+fallback, and importing this module fails loudly if the library is missing.
+
+The functions mirror the C ABI in ``include/bbp.h`` (same names); ``Plan`` is a
+small convenience wrapper around a ``bbp_plan`` handle.  Device buffers and
+streams may come from PyTorch (``tensor.data_ptr()``, ``stream.cuda_stream``);
+this module itself never imports torch.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbbp.so")
+
+BBP_OK = 0
+BBP_PENDING = 1
+BBP_EINVAL = -1
+BBP_ENOMEM = -2
+BBP_ECUDA = -3
+BBP_EBUSY = -4
+BBP_ETIMEOUT = -5
+BBP_ERANGE = -6
+BBP_EINVALID_BITS = -7
+BBP_ENOTFOUND = -8
+
+BBP_BELLARD = 0
+BBP_BBP = 1
+UINT64_MAX = (1 << 64) - 1
+
+
+class BBPError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {bbp_status_str(status)} ({status})" if what else bbp_status_str(status))
+
+
+class bbp_plan_opts(ctypes.Structure):
+    _fields_ = [
+        ("device", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+        ("guard_bits", ctypes.c_uint32),
+        ("accum_mem_budget", ctypes.c_size_t),
+        ("max_slots", ctypes.c_uint32),
+        ("tune_table", ctypes.c_char_p),
+        ("profile", ctypes.c_uint32),
+        ("strict", ctypes.c_uint32),
+    ]
+
+
+class bbp_stats(ctypes.Structure):
+    _fields_ = [
+        ("terms", ctypes.c_uint64),
+        ("head_terms", ctypes.c_uint64),
+        ("head_launches", ctypes.c_uint64),
+        ("kernel_launches", ctypes.c_uint64),
+        ("imad_model", ctypes.c_double),
+        ("head_ms", ctypes.c_double),
+    ]
+
+
+def build(verbose: bool = False, force: bool = False) -> str:
+    """Compile libbbp.so for sm_103a in-tree (nvcc; needs no GPU)."""
+    from . import _build
+
+    return _build.build(verbose=verbose, force=force)
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"libbbp.so not found at {LIB_PATH}: build it first "
+            "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(LIB_PATH)
+    u32, u64, vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    u64p = ctypes.POINTER(ctypes.c_uint64)
+    sig = {
+        "bbp_abi_version": ([], u32),
+        "bbp_status_str": ([ctypes.c_int], ctypes.c_char_p),
+        "bbp_plan_opts_default": ([ctypes.POINTER(bbp_plan_opts)], None),
+        "bbp_plan_create": ([ctypes.POINTER(vp), ctypes.POINTER(bbp_plan_opts)], ctypes.c_int),
+        "bbp_plan_destroy": ([vp], ctypes.c_int),
+        "bbp_working_bits": ([vp, u32], u32),
+        "bbp_series_extent": ([ctypes.c_int, u32, u64, u32, u64p, u64p], ctypes.c_int),
+        "bbp_partial_sum": ([vp, ctypes.c_int, u32, u64, u64, u64, u32, u32p], ctypes.c_int),
+        "bbp_partial_sum_async": ([vp, ctypes.c_int, u32, u64, u64, u64, u32, vp, vp], ctypes.c_int),
+        "bbp_bits": ([vp, u64, u32, ctypes.c_char_p, u32p], ctypes.c_int),
+        "bbp_bits_formula": ([vp, ctypes.c_int, u64, u32, ctypes.c_char_p, u32p], ctypes.c_int),
+        "bbp_bits_async": ([vp, ctypes.c_int, u64, u32, vp, vp, vp, vp], ctypes.c_int),
+        "bbp_plan_stats": ([vp, ctypes.POINTER(bbp_stats)], ctypes.c_int),
+        "bbp_imad_probe": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+_lib = _load()
+
+
+def _check(status: int, what: str) -> int:
+    if status < 0:
+        raise BBPError(status, what)
+    return status
+
+
+# ---------------------------------------------------------------- ABI-named functions
+
+def bbp_abi_version() -> int:
+    return _lib.bbp_abi_version()
+
+
+def bbp_status_str(status: int) -> str:
+    return _lib.bbp_status_str(status).decode()
+
+
+def bbp_plan_create(device: int = 0, stream: Optional[int] = None, guard_bits: int = 64,
+                    accum_mem_budget: int = 0, max_slots: int = 0, tune_table: Optional[str] = None,
+                    profile: bool = False, strict: bool = False) -> int:
+    opts = bbp_plan_opts()
+    _lib.bbp_plan_opts_default(ctypes.byref(opts))
+    opts.device = device
+    opts.stream = stream or None
+    opts.guard_bits = guard_bits
+    opts.accum_mem_budget = accum_mem_budget
+    opts.max_slots = max_slots
+    opts.tune_table = tune_table.encode() if tune_table else None
+    opts.profile = 1 if profile else 0
+    opts.strict = 1 if strict else 0
+    handle = ctypes.c_void_p()
+    _check(_lib.bbp_plan_create(ctypes.byref(handle), ctypes.byref(opts)), "bbp_plan_create")
+    return handle.value
+
+
+def bbp_plan_destroy(plan: int) -> None:
+    _check(_lib.bbp_plan_destroy(plan), "bbp_plan_destroy")
+
+
+def bbp_working_bits(plan: int, P: int) -> int:
+    return _lib.bbp_working_bits(plan, P)
+
+
+def bbp_series_extent(formula: int, denominator: int, n: int, W: int) -> tuple[int, int]:
+    he, ne = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(_lib.bbp_series_extent(formula, denominator, n, W, ctypes.byref(he), ctypes.byref(ne)),
+           "bbp_series_extent")
+    return he.value, ne.value
+
+
+def bbp_partial_sum(plan: int, formula: int, denominator: int, k_begin: int, k_end: Optional[int],
+                    n: int, P: int) -> list[int]:
+    """W/32 little-endian limbs of sign_j * sum_k (-1)^k t_{j,k} mod 2^W."""
+    W = bbp_working_bits(plan, P)
+    if W == 0:
+        raise BBPError(BBP_EINVAL, "bbp_partial_sum")
+    out = (ctypes.c_uint32 * (W // 32))()
+    _check(_lib.bbp_partial_sum(plan, formula, denominator, k_begin, UINT64_MAX if k_end is None else k_end,
+                                n, P, out), "bbp_partial_sum")
+    return list(out)
+
+
+def bbp_partial_sum_async(plan: int, formula: int, denominator: int, k_begin: int, k_end: Optional[int],
+                          n: int, P: int, d_out_limbs: int, stream: Optional[int] = None) -> None:
+    _check(_lib.bbp_partial_sum_async(plan, formula, denominator, k_begin,
+                                      UINT64_MAX if k_end is None else k_end, n, P, d_out_limbs, stream or None),
+           "bbp_partial_sum_async")
+
+
+def bbp_bits_formula(plan: int, formula: int, n: int, P: int) -> tuple[bytes, int]:
+    """(ceil(P/8) MSB-first bytes of bits n..n+P-1, certified bit count)."""
+    out = ctypes.create_string_buffer((P + 7) // 8)
+    valid = ctypes.c_uint32()
+    st = _lib.bbp_bits_formula(plan, formula, n, P, out, ctypes.byref(valid))
+    if st == BBP_EINVALID_BITS:
+        raise BBPError(st, f"bbp_bits_formula (certified {valid.value} of {P})")
+    _check(st, "bbp_bits_formula")
+    return out.raw, valid.value
+
+
+def bbp_bits(plan: int, n: int, P: int) -> tuple[bytes, int]:
+    return bbp_bits_formula(plan, BBP_BELLARD, n, P)
+
+
+def bbp_bits_async(plan: int, formula: int, n: int, P: int, d_out: int, d_valid: int = 0, d_limbs: int = 0,
+                   stream: Optional[int] = None) -> None:
+    _check(_lib.bbp_bits_async(plan, formula, n, P, d_out, d_valid or None, d_limbs or None, stream or None),
+           "bbp_bits_async")
+
+
+def bbp_plan_stats(plan: int) -> dict:
+    st = bbp_stats()
+    _check(_lib.bbp_plan_stats(plan, ctypes.byref(st)), "bbp_plan_stats")
+    return {name: getattr(st, name) for name, _ in bbp_stats._fields_}
+
+
+def bbp_imad_probe(plan: int, kind: int) -> float:
+    v = ctypes.c_double()
+    _check(_lib.bbp_imad_probe(plan, kind, ctypes.byref(v)), "bbp_imad_probe")
+    return v.value
+
+
+# ---------------------------------------------------------------- convenience wrapper
+
+def limbs_to_int(limbs) -> int:
+    return sum(int(v) << (32 * i) for i, v in enumerate(limbs))
+
+
+class Plan:
+    """Owns one bbp_plan handle (closed on ``close()`` or garbage collection)."""
+
+    def __init__(self, **opts):
+        self.handle = bbp_plan_create(**opts)
+
+    def close(self) -> None:
+        if self.handle:
+            bbp_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def working_bits(self, P: int) -> int:
+        return bbp_working_bits(self.handle, P)
+
+    def partial_sum(self, formula: int, denominator: int, k_begin: int, k_end: Optional[int], n: int,
+                    P: int) -> int:
+        return limbs_to_int(bbp_partial_sum(self.handle, formula, denominator, k_begin, k_end, n, P))
+
+    def bits(self, n: int, P: int, formula: int = BBP_BELLARD) -> tuple[int, int]:
+        """(the P bits as an integer, MSB = bit n; certified bit count)."""
+        raw, valid = bbp_bits_formula(self.handle, formula, n, P)
+        return int.from_bytes(raw, "big") >> (8 * len(raw) - P), valid
+
+    def stats(self) -> dict:
+        return bbp_plan_stats(self.handle)
+
+    def imad_probe(self, kind: int) -> float:
+        return bbp_imad_probe(self.handle, kind)

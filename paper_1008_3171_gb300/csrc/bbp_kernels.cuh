@@ -1,0 +1,59 @@
+// Kernel argument blocks and host-side launch wrappers shared by the runtime.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bbp {
+
+// One contiguous run of head terms (exponent e >= 0) of one series:
+// k in [k_begin, k_begin + count), m = a k + b, e = d + c - step k.
+struct HeadArgs {
+  uint64_t d;            // n - 1
+  uint64_t k_begin;      // first term index
+  uint64_t count;        // number of terms (> 0)
+  uint32_t a, b;         // modulus m = a k + b (odd)
+  int32_t c;             // exponent offset of the series
+  uint32_t step;         // exponent decrease per k (10 or 4)
+  uint32_t W;            // working bits, 32 L
+  uint32_t L;            // limbs
+  uint32_t alternating;  // 1 if the series carries (-1)^k
+  uint32_t negate;       // 1 if this run's partial enters the sum negated
+  uint32_t run;          // consecutive terms per stream (even)
+  uint32_t window;       // ladder window bits (>= 1)
+  uint32_t first;        // bits taken by the first window (0 allowed)
+  unsigned long long* slots;  // L carry-save accumulators, limb i at slots[i]
+};
+
+// Tail terms (e < 0): t = floor(2^(W+e) / m), one thread per term.
+struct TailArgs {
+  uint64_t d;
+  uint64_t k_begin;
+  uint64_t count;
+  uint32_t a, b;
+  int32_t c;
+  uint32_t step;
+  uint32_t W;
+  uint32_t L;
+  uint32_t alternating;
+  uint32_t negate;
+  unsigned long long* slots;
+};
+
+constexpr int kMaxLimbs = 40;    // W <= 1280 bits
+constexpr int kHeadThreads = 256;
+
+// Launch helpers (defined in bbp_kernels.cu).  They return cudaGetLastError().
+// variant: 0 = 32-bit modulus path (m < 2^29), 1 = 64-bit path (m < 2^60).
+cudaError_t launch_head(const HeadArgs& a, int wide, int streams, int lmax, int blocks, cudaStream_t s);
+cudaError_t launch_tail(const TailArgs& a, cudaStream_t s);
+cudaError_t launch_zero_slots(unsigned long long* slots, int L, cudaStream_t s);
+cudaError_t launch_fold_limbs(const unsigned long long* slots, int L, uint32_t* out_limbs, cudaStream_t s);
+cudaError_t launch_finalize_bits(const unsigned long long* slots, int L, uint32_t P, uint64_t bound,
+                                 uint8_t* out_bytes, uint32_t* valid_bits, uint32_t* out_limbs, cudaStream_t s);
+int head_lmax_for(int L);  // smallest compiled limb capacity >= L, or 0
+int head_occupancy(int wide, int streams, int lmax);  // resident CTAs per SM of that instantiation
+cudaError_t launch_imad_probe(int kind, int blocks, int threads, int iters, unsigned long long* cycles_out,
+                              uint32_t* smid_out, uint32_t* sink, cudaStream_t s);
+
+}  // namespace bbp

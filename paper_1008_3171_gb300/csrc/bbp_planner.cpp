@@ -1,0 +1,186 @@
+// Host-side query planning for BBP digit extraction (Sze, arXiv:1008.3171, Sec. 3).
+#include "bbp_planner.h"
+
+#include <algorithm>
+#include <limits>
+
+namespace bbp {
+
+namespace {
+// Eq. 2: 2^2/(10k+1) - 1/(10k+3) - 2^-4/(10k+5) - 2^-4/(10k+7) + 2^-6/(10k+9)
+//        - 2^-1/(4k+1) - 2^-6/(4k+3), times (-1)^k 2^-10k.
+// Eq. 1 as in Eq. 3: 2^2/(8k+1) - 2^-1/(2k+1) - 1/(8k+5) - 2^-1/(4k+3), times 2^-4k.
+const FormulaDef kFormulas[2] = {
+    {10, 1, 7, {{10, 1, +1, 2}, {10, 3, -1, 0}, {10, 5, -1, -4}, {10, 7, -1, -4},
+                {10, 9, +1, -6}, {4, 1, -1, -1}, {4, 3, -1, -6}}},
+    {4, 0, 4, {{8, 1, +1, 2}, {2, 1, -1, -1}, {8, 5, -1, 0}, {4, 3, -1, -1}}},
+};
+
+int64_t floor_div(int64_t a, int64_t b) {  // b > 0
+  int64_t q = a / b;
+  if ((a % b) != 0 && a < 0) --q;
+  return q;
+}
+
+int64_t ceil_div(int64_t a, int64_t b) { return -floor_div(-a, b); }
+
+// first k >= 0 with a k + b >= v
+uint64_t first_k_at_least(uint64_t v, uint32_t a, uint32_t b) {
+  if (v <= b) return 0;
+  return (v - b + a - 1) / a;
+}
+
+constexpr uint64_t kMinRangeTerms = 1ull << 16;
+}  // namespace
+
+const FormulaDef& formula_def(int f) { return kFormulas[f == 1 ? 1 : 0]; }
+
+int bitlen(uint64_t v) {
+  int n = 0;
+  while (v) { ++n; v >>= 1; }
+  return n;
+}
+
+bool working_bits(uint32_t P, uint32_t G, uint32_t* W) {
+  if (P == 0 || G == 0 || G % 32 != 0) return false;
+  const uint64_t w = (static_cast<uint64_t>(P) + 31) / 32 * 32 + G;
+  if (w > kMaxWorkingBits) return false;
+  *W = static_cast<uint32_t>(w);
+  return true;
+}
+
+uint64_t head_end(const FormulaDef& f, uint32_t j, uint64_t d) {
+  const int64_t top = static_cast<int64_t>(d) + f.s[j].c;
+  return top < 0 ? 0 : static_cast<uint64_t>(top) / f.step + 1;
+}
+
+uint64_t natural_end(const FormulaDef& f, uint32_t j, uint64_t d, uint32_t W) {
+  const SeriesDef& s = f.s[j];
+  for (uint64_t k = head_end(f, j, d);; ++k) {
+    const int64_t p = static_cast<int64_t>(W) + static_cast<int64_t>(d) + s.c - static_cast<int64_t>(f.step * k);
+    if (p < 0) return k;
+    const uint64_t m = static_cast<uint64_t>(s.a) * k + s.b;
+    if (p < 64 && (1ull << p) < m) return k;  // floor(2^p / m) == 0
+  }
+}
+
+void window_params(bool wide, int lbits, uint8_t* window, uint8_t* first) {
+  // shifted reduction keeps x < 2m while lbits + s <= 61 (64-bit) / <= 30 (32-bit);
+  // the first window (x = (R mod m) << w0) needs lbits + 2 w0 + 1 <= 64 / 32.
+  const int shift_cap = wide ? 61 - lbits : 30 - lbits;
+  const int rbits = wide ? 64 : 32;
+  int w = 0;
+  while (w < 4 && (1 << (w + 1)) - 1 <= shift_cap) ++w;
+  int h = 0;
+  while (h < 4 && lbits + 2 * ((1 << (h + 1)) - 1) + 1 <= rbits) ++h;
+  *window = static_cast<uint8_t>(w);
+  *first = static_cast<uint8_t>(h);
+}
+
+double head_term_imad(bool wide, int nb, int first, int lmax) {
+  const int h = nb > 0 ? std::min(first, nb - 1) : 0;
+  const int sq = nb - h;
+  return wide ? 16.0 * sq + 5.0 * lmax + 8.0 : 4.0 * sq + 2.0 * lmax + 8.0;
+}
+
+namespace {
+double range_imad(const FormulaDef& f, const SeriesDef& s, uint64_t d, uint32_t W, const TermRange& r, int lmax) {
+  const int rb = r.wide ? 64 : 32;
+  const int64_t v0 = static_cast<int64_t>(d) + s.c + static_cast<int64_t>(W) - rb;  // v at k = 0
+  const int64_t k_lo = static_cast<int64_t>(r.k_begin);
+  const int64_t k_hi = static_cast<int64_t>(r.k_begin + r.count) - 1;
+  double total = 0;
+  for (int i = 0; i < 64; ++i) {
+    const int64_t lo_v = i == 0 ? 0 : (int64_t{1} << (i - 1));
+    const int64_t hi_v = i == 0 ? 0 : (i == 63 ? std::numeric_limits<int64_t>::max() : (int64_t{1} << i) - 1);
+    // lo_v <= v0 - step k <= hi_v
+    const int64_t ka = std::max(k_lo, ceil_div(v0 - hi_v, f.step));
+    const int64_t kb = std::min(k_hi, floor_div(v0 - lo_v, f.step));
+    if (kb >= ka) total += static_cast<double>(kb - ka + 1) * head_term_imad(r.wide, i, r.first, lmax);
+  }
+  return total;
+}
+}  // namespace
+
+int plan_series(const FormulaDef& f, uint32_t j, uint64_t n, uint32_t W, uint32_t lmax, uint64_t k_lo,
+                uint64_t k_hi, std::vector<TermRange>& out) {
+  if (n == 0 || j >= f.count || W == 0 || W % 32 != 0 || W > kMaxWorkingBits) return -1;
+  const SeriesDef& s = f.s[j];
+  const uint64_t d = n - 1;
+  const uint64_t he = head_end(f, j, d);
+  const uint64_t ne = natural_end(f, j, d, W);
+  const uint64_t hi = std::min(k_hi, ne);
+  if (k_lo >= hi) return 0;
+  if (static_cast<uint64_t>(s.a) * (hi - 1) + s.b >= (1ull << kMaxModulusBits)) return -6;
+
+  // head terms, k in [head_lo, head_hi); the term with m = 1 is 0 (2^e mod 1 = 0)
+  const uint64_t head_lo = std::max(k_lo, s.b == 1 ? uint64_t{1} : uint64_t{0});
+  const uint64_t head_hi = std::min(hi, he);
+  if (head_lo < head_hi) {
+    struct Group { uint64_t k0, k1; int lmax_bits; bool wide; uint8_t w, h; };
+    std::vector<Group> groups;
+    const int l_first = bitlen(static_cast<uint64_t>(s.a) * head_lo + s.b);
+    const int l_last = bitlen(static_cast<uint64_t>(s.a) * (head_hi - 1) + s.b);
+    for (int l = l_first; l <= l_last; ++l) {
+      uint64_t k0 = std::max(head_lo, first_k_at_least(1ull << (l - 1), s.a, s.b));
+      uint64_t k1 = std::min(head_hi, first_k_at_least(1ull << l, s.a, s.b));
+      if (k0 >= k1) continue;
+      const bool wide = l >= kWideMinBits;
+      uint8_t w, h;
+      window_params(wide, l, &w, &h);
+      if (!groups.empty() && groups.back().wide == wide && groups.back().w == w && groups.back().h == h &&
+          groups.back().k1 == k0) {
+        groups.back().k1 = k1;
+        groups.back().lmax_bits = l;
+      } else {
+        groups.push_back(Group{k0, k1, l, wide, w, h});
+      }
+    }
+    // fold small groups into their larger-modulus neighbour (whose parameters are
+    // valid for smaller moduli too) to keep the launch count down
+    std::vector<Group> merged;
+    for (size_t i = 0; i < groups.size(); ++i) {
+      Group g = groups[i];
+      while (g.k1 - g.k0 < kMinRangeTerms && i + 1 < groups.size() && groups[i + 1].wide == g.wide) {
+        const Group& nx = groups[++i];
+        g.k1 = nx.k1;
+        g.lmax_bits = nx.lmax_bits;
+        g.w = nx.w;
+        g.h = nx.h;
+      }
+      if (!merged.empty() && g.k1 - g.k0 < kMinRangeTerms && merged.back().wide == g.wide) {
+        merged.back().k1 = g.k1;
+        merged.back().lmax_bits = g.lmax_bits;
+        merged.back().w = g.w;
+        merged.back().h = g.h;
+      } else {
+        merged.push_back(g);
+      }
+    }
+    for (const Group& g : merged) {
+      TermRange r{};
+      r.j = j;
+      r.tail = 0;
+      r.wide = g.wide ? 1 : 0;
+      r.window = g.w;
+      r.first = g.h;
+      r.k_begin = g.k0;
+      r.count = g.k1 - g.k0;
+      r.imad = range_imad(f, s, d, W, r, static_cast<int>(lmax));
+      out.push_back(r);
+    }
+  }
+  // tail terms, k in [max(k_lo, head_end), hi)
+  const uint64_t tail_lo = std::max(k_lo, he);
+  if (tail_lo < hi) {
+    TermRange r{};
+    r.j = j;
+    r.tail = 1;
+    r.k_begin = tail_lo;
+    r.count = hi - tail_lo;
+    out.push_back(r);
+  }
+  return 0;
+}
+
+}  // namespace bbp

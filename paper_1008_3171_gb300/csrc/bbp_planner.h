@@ -1,0 +1,64 @@
+// Host-side planning of a BBP query: which terms exist, how they split into
+// kernel ranges, and what each range costs.  Pure C++, no CUDA.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+namespace bbp {
+
+struct SeriesDef {
+  uint32_t a, b;  // modulus m = a k + b
+  int32_t sign;   // +1 / -1 in front of the series
+  int32_t c;      // exponent offset: the series term is 2^(d + c - step k) / m
+};
+
+struct FormulaDef {
+  uint32_t step;         // exponent decrease per k
+  uint32_t alternating;  // (-1)^k factor
+  uint32_t count;        // number of series
+  SeriesDef s[7];
+};
+
+// Eq. 2 (index 0) and Eq. 1 in the form of Eq. 3 (index 1).
+const FormulaDef& formula_def(int f);
+
+constexpr uint32_t kMaxWorkingBits = 1280;   // 40 limbs
+constexpr int kWideMinBits = 30;             // moduli with bitlen >= 30 take the 64-bit path
+constexpr int kMaxModulusBits = 60;          // 64-bit path bound
+
+// A contiguous run of terms of one series with one kernel configuration.
+struct TermRange {
+  uint32_t j;         // series index
+  uint8_t tail;       // 0 head (e >= 0), 1 tail (e < 0)
+  uint8_t wide;       // head: 64-bit modulus path
+  uint8_t window;     // head: ladder window bits
+  uint8_t first;      // head: first-window bits
+  uint64_t k_begin;   // first k
+  uint64_t count;     // number of terms
+  double imad;        // modelled multiply instructions for the range (head only)
+};
+
+int bitlen(uint64_t v);
+
+// W = roundup(P, 32) + G; false when out of range.
+bool working_bits(uint32_t P, uint32_t G, uint32_t* W);
+
+// First k with exponent < 0 (Eq. 4 split) and the natural end of the tail.
+uint64_t head_end(const FormulaDef& f, uint32_t j, uint64_t d);
+uint64_t natural_end(const FormulaDef& f, uint32_t j, uint64_t d, uint32_t W);
+
+// Ladder parameters for moduli of at most `lbits` bits on the given path.
+void window_params(bool wide, int lbits, uint8_t* window, uint8_t* first);
+
+// Modelled 32-bit multiply instructions of one head term whose ladder exponent
+// has nb bits (see the kernel): per squaring 16 (64-bit) or 4 (32-bit), per
+// quotient digit 5 or 2, plus 8 for the inverse.
+double head_term_imad(bool wide, int nb, int first, int lmax);
+
+// Appends the ranges of series j restricted to k in [k_lo, k_hi) (k_hi = UINT64_MAX:
+// natural end).  Returns 0, or -6 (modulus too large) / -1 (bad argument).
+int plan_series(const FormulaDef& f, uint32_t j, uint64_t n, uint32_t W, uint32_t lmax, uint64_t k_lo,
+                uint64_t k_hi, std::vector<TermRange>& out);
+
+}  // namespace bbp

@@ -1,0 +1,47 @@
+// Internal state of a bbp_plan, shared by the runtime translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "bbp.h"
+#include "bbp_planner.h"
+
+struct bbp_plan_s {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  uint32_t guard = 64;
+  bool profile = false;
+  bool strict = false;
+  size_t accum_budget = 0;
+  uint32_t max_slots = 0;
+  int sm_count = 0;
+  // head-kernel tuning (terms per stream run, streams per thread)
+  int run = 32;
+  int streams = 1;
+  // single-query buffers
+  unsigned long long* d_slots = nullptr;  // kMaxLimbs carry-save accumulators
+  uint32_t* d_limbs = nullptr;
+  uint8_t* d_bytes = nullptr;
+  uint32_t* d_valid = nullptr;
+  void* h_stage = nullptr;  // 4 KiB pinned staging
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bbp_stats stats{};
+  // batched / serving state (bbp_batch.cu)
+  struct BatchState* batch = nullptr;
+};
+
+namespace bbp {
+
+bbp_status cuda_status(cudaError_t e);
+bbp_status plan_query(int f, uint64_t n, uint32_t W, int j_only, uint64_t k_lo, uint64_t k_hi,
+                      std::vector<TermRange>& ranges, uint64_t* n_terms);
+bbp_status launch_ranges(bbp_plan p, int f, uint64_t n, uint32_t W, const std::vector<TermRange>& ranges,
+                         unsigned long long* slots, cudaStream_t st);
+void load_tune_table(bbp_plan p, const char* path);
+void release_batch_state(bbp_plan p);
+
+}  // namespace bbp
