@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Benchmark: BBP digit extraction of pi, n = 1e12, P = 256 (+64 guard bits), one GB300.
+
+One step is one whole query: every series of Bellard's formula (Eq. 2), head and
+tail terms, the exact reduction and the finalize (certified bits + output bytes),
+through the library's public API with host output buffers.  The device time of a
+step comes from CUDA events on the plan's stream; the end-to-end time is the
+wall clock around the same API call (it includes the device->host read of the
+result).  Between timed steps the L2 is flushed by writing a 256 MiB buffer.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+N > 1 (torchrun, one rank per GPU): each rank evaluates its shard of every
+series (bbp_shard_range), the carry-save partial sums are summed exactly with one
+all-reduce, and rank 0 finalizes -- total work fixed, so scaling is "strong".
+
+--impl reference times the oracle (plain C, all host cores) on a bounded sample
+of the same query: evenly spaced k-ranges of every series' head.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_POS = 10**12
+P_BITS = 256
+GUARD = 64
+METRIC = "BBP terms/s at n=1e12 P=256; % of INT32 IMAD peak; batched p50/p99 latency"
+WORKLOAD = "plain single query: Bellard formula, n=1e12, P=256 + 64 guard bits, all 7 series"
+IMAD_LANES_PER_CLK_PER_SM = 64     # 32-bit multiply-add (low half) issue rate per SM, measured by bbp_imad_probe
+SM_MAX_MHZ_FALLBACK = 2070.0       # GB300 maximum SM clock
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target wall time of one oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- oracle sample (CPU)
+
+def oracle_sample(n: int, P: int, G: int, target_s: float, threads: int = 0):
+    """Times oracle O2 on evenly spaced k-ranges of every series' head terms.
+
+    Returns (terms, seconds, description).  The per-term cost is nearly constant
+    across the head (it grows with the exponent's bit length), so evenly spaced
+    ranges estimate the whole query's rate; the tail terms are negligible."""
+    import oracle
+    from oracle import bbp_oracle as o1
+
+    f = o1.BELLARD
+    W = o1.working_bits(P, G)
+    positions = 16
+
+    def run(span):
+        total = 0
+        t0 = time.perf_counter()
+        for j, s in enumerate(f.series):
+            he = o1.head_end(f, s, n - 1)
+            for i in range(positions):
+                kb = 1 + (he - span - 2) * i // (positions - 1)
+                oracle.c_partial_sum(0, j, kb, kb + span, n, P, G, threads)
+                total += span
+        return total, time.perf_counter() - t0
+
+    terms, secs = run(2000)                      # calibration
+    rate = terms / max(secs, 1e-6)
+    span = max(2000, int(rate * target_s / (len(f.series) * positions)))
+    terms, secs = run(span)
+    desc = (f"oracle O2 (plain C, 128-bit integers) on {len(f.series)} series x {positions} evenly spaced "
+            f"head k-ranges of {span} terms ({terms} terms) of the n={n}, P={P}, G={G} query")
+    return terms, secs, desc
+
+
+def host_cores() -> int:
+    return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="bbp_clocks_", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1])]
+        smax = [num(r[2]) for r in rows if num(r[2])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        loaded = [v for v in sm if smax and v > 0.5 * max(smax)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- distributed
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def emit(obj):
+    print(json.dumps(obj), flush=True)
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:           # under torchrun only rank 0 runs and prints the reference arm
+        return
+    # each step: one bounded oracle sample of the same workload
+    per_step = max(2.0, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample(N_POS, P_BITS, GUARD, per_step)
+    terms = 0
+    secs = 0.0
+    desc = ""
+    for _ in range(args.steps):
+        t, s, desc = oracle_sample(N_POS, P_BITS, GUARD, per_step)
+        terms += t
+        secs += s
+    value = terms / secs
+    emit({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "terms/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_POS, "P": P_BITS, "guard_bits": GUARD,
+                   "sample": "bounded oracle sample per step"},
+        "cpu_baseline": {"value": value, "unit": "terms/s", "cores": host_cores(), "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "terms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    })
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def expected_bits_check(bits_value: int, valid: int) -> bool:
+    """Bits 2..256 at n = 1e12 equal the first 255 bits of the paper's row for
+    n = 1e12 + 1 (Table 2 source, suppressed m = 12 row)."""
+    with open(os.path.join(ROOT, "tests", "golden", "paper_pins.json")) as fh:
+        pins = {p["name"]: p for p in json.load(fh)["pins"]}
+    row = pins["suppressed_m12"]
+    ref = int(row["hex"], 16) >> (4 * len(row["hex"]) - row["bits"])
+    return valid == P_BITS and (bits_value & ((1 << 255) - 1)) == ref >> (row["bits"] - 255)
+
+
+def run_gpu(args):
+    import torch
+
+    import paper_1008_3171_gb300 as bbp
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.current_stream()
+    plan = bbp.Plan(device=local, stream=stream.cuda_stream, guard_bits=GUARD, profile=True)
+    W = plan.working_bits(P_BITS)
+    L = W // 32
+    nbytes = (P_BITS + 7) // 8
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    slots = torch.zeros(L, dtype=torch.int64, device=dev)
+    d_out = torch.zeros(nbytes, dtype=torch.uint8, device=dev)
+    d_valid = torch.zeros(1, dtype=torch.int32, device=dev)
+    out_host = torch.zeros(nbytes + 4, dtype=torch.uint8).pin_memory()
+
+    def step_single():
+        raw, valid = bbp.bbp_bits(plan.handle, N_POS, P_BITS)
+        return int.from_bytes(raw, "big"), valid
+
+    def step_sharded():
+        slots.zero_()
+        bbp.bbp_accumulate_async(plan.handle, 0, N_POS, P_BITS, rank, world, slots.data_ptr(), stream.cuda_stream)
+        dist.all_reduce(slots)
+        if rank == 0:
+            bbp.bbp_finalize_async(plan.handle, 0, N_POS, P_BITS, slots.data_ptr(), d_out.data_ptr(),
+                                   d_valid.data_ptr(), 0, stream.cuda_stream)
+            out_host[:nbytes].copy_(d_out, non_blocking=True)
+            out_host[nbytes:].copy_(d_valid.view(torch.uint8), non_blocking=True)
+        torch.cuda.synchronize()
+        if rank == 0:
+            raw = bytes(out_host[:nbytes].tolist())
+            valid = int.from_bytes(bytes(out_host[nbytes:].tolist()), "little")
+            return int.from_bytes(raw, "big"), valid
+        return None, None
+
+    step = step_single if world == 1 else step_sharded
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    dev_ms = []
+    wall_s = []
+    head_ms = 0.0
+    imad = 0.0
+    head_launches = 0
+    launches = 0
+    terms = 0
+    verified = True
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)             # L2 flush, outside the timed events
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        v, valid = step()
+        e1.record(stream)
+        t1 = time.perf_counter()
+        e1.synchronize()
+        dev_ms.append(e0.elapsed_time(e1))
+        wall_s.append(t1 - t0)
+        st = plan.stats()
+        head_ms += st["head_ms"]
+        imad += st["imad_model"]
+        head_launches += st["head_launches"]
+        launches += st["kernel_launches"] + (1 if world > 1 and rank == 0 else 0)
+        terms += st["terms"]
+        if rank == 0:
+            verified = verified and expected_bits_check(v, valid)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+
+    # whole-job numbers: max time over ranks, all ranks' terms
+    t_dev = sum(dev_ms) / 1e3
+    t_e2e = sum(wall_s)
+    if world > 1:
+        agg = torch.tensor([t_dev, t_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(agg, op=dist.ReduceOp.MAX)
+        t_dev, t_e2e = agg.tolist()
+        tt = torch.tensor([terms, launches], dtype=torch.int64, device=dev)
+        dist.all_reduce(tt)
+        terms, launches = tt.tolist()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    max_mhz = (clocks or {}).get("sm_max_mhz") or SM_MAX_MHZ_FALLBACK
+    peak = sms * IMAD_LANES_PER_CLK_PER_SM * max_mhz * 1e6 / 1e12        # T multiply instructions / s
+    achieved = (imad / (head_ms / 1e3)) / 1e12 if head_ms > 0 else None
+    value = terms / t_dev
+    e2e_value = terms / t_e2e
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        c_terms, c_secs, desc = oracle_sample(N_POS, P_BITS, GUARD, args.cpu_seconds)
+        cpu = {"value": c_terms / c_secs, "unit": "terms/s", "cores": host_cores(), "kind": "oracle", "sample": desc}
+
+    emit({
+        "metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_POS, "P": P_BITS, "guard_bits": GUARD,
+                   "terms_per_step": terms // args.steps, "l2": "flushed (256 MiB write) between steps",
+                   "parallelism": f"k-range shards x{world}" if world > 1 else "single GPU"},
+        "e2e": {"value": e2e_value, "unit": "terms/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": nbytes + 4,
+                "note": "bbp_bits with host output; the query (n, P) travels as kernel arguments"},
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T IMAD/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "kernel": "head_kernel", "head_launches": head_launches,
+                     "peak_basis": f"{sms} SMs x {IMAD_LANES_PER_CLK_PER_SM} IMAD lanes/clk x {max_mhz:.0f} MHz"},
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "verified": verified,
+    })
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -130,6 +130,30 @@ bbp_status bbp_bits_formula(bbp_plan p, bbp_formula f, uint64_t n, uint32_t P, u
 bbp_status bbp_bits_async(bbp_plan p, bbp_formula f, uint64_t n, uint32_t P, uint8_t* d_out,
                           uint32_t* d_valid, uint32_t* d_limbs, void* stream);
 
+/* Host-only split of series j's terms [0, natural_end) into nshards contiguous
+ * shards: the head range is cut evenly, the tail goes to the last shard.
+ * Writes shard `shard`'s range [*k_begin, *k_end).  Needs no GPU. */
+bbp_status bbp_shard_range(bbp_formula f, uint32_t denominator, uint64_t n, uint32_t W, uint32_t shard,
+                           uint32_t nshards, uint64_t* k_begin, uint64_t* k_end);
+
+/* Adds shard `shard` of `nshards` of the whole query (every series, ranges from
+ * bbp_shard_range) into caller-owned device carry-save accumulators
+ * d_slots[0..W/32): limb i of the signed sum is added to d_slots[i] (uint64).
+ * The caller zeroes d_slots once; the sum over all shards (added on one device,
+ * or added limb-wise across devices, exact while fewer than 2^31 shards) is the
+ * query's sum S mod 2^W in carry-save form.  Queued on `stream`; does not block.
+ * This is also the checkpoint unit: slots saved after some shards resume by
+ * adding the remaining shards. */
+bbp_status bbp_accumulate_async(bbp_plan p, bbp_formula f, uint64_t n, uint32_t P, uint32_t shard,
+                                uint32_t nshards, unsigned long long* d_slots, void* stream);
+
+/* Turns carry-save accumulators holding a whole query's sum into output bits
+ * (d_out, ceil(P/8) bytes), the certified count (d_valid, may be NULL) and the
+ * raw sum (d_limbs, W/32 uint32, may be NULL); all caller-owned device memory. */
+bbp_status bbp_finalize_async(bbp_plan p, bbp_formula f, uint64_t n, uint32_t P,
+                              const unsigned long long* d_slots, uint8_t* d_out, uint32_t* d_valid,
+                              uint32_t* d_limbs, void* stream);
+
 /* Counters of the last compute call on this plan. */
 bbp_status bbp_plan_stats(bbp_plan p, bbp_stats* out);
 

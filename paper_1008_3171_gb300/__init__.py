@@ -95,6 +95,9 @@ def _load():
         "bbp_bits_formula": ([vp, ctypes.c_int, u64, u32, ctypes.c_char_p, u32p], ctypes.c_int),
         "bbp_bits_async": ([vp, ctypes.c_int, u64, u32, vp, vp, vp, vp], ctypes.c_int),
         "bbp_plan_stats": ([vp, ctypes.POINTER(bbp_stats)], ctypes.c_int),
+        "bbp_shard_range": ([ctypes.c_int, u32, u64, u32, u32, u32, u64p, u64p], ctypes.c_int),
+        "bbp_accumulate_async": ([vp, ctypes.c_int, u64, u32, u32, u32, vp, vp], ctypes.c_int),
+        "bbp_finalize_async": ([vp, ctypes.c_int, u64, u32, vp, vp, vp, vp, vp], ctypes.c_int),
         "bbp_imad_probe": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -194,6 +197,25 @@ def bbp_bits_async(plan: int, formula: int, n: int, P: int, d_out: int, d_valid:
                    stream: Optional[int] = None) -> None:
     _check(_lib.bbp_bits_async(plan, formula, n, P, d_out, d_valid or None, d_limbs or None, stream or None),
            "bbp_bits_async")
+
+
+def bbp_shard_range(formula: int, denominator: int, n: int, W: int, shard: int, nshards: int) -> tuple[int, int]:
+    kb, ke = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(_lib.bbp_shard_range(formula, denominator, n, W, shard, nshards, ctypes.byref(kb), ctypes.byref(ke)),
+           "bbp_shard_range")
+    return kb.value, ke.value
+
+
+def bbp_accumulate_async(plan: int, formula: int, n: int, P: int, shard: int, nshards: int, d_slots: int,
+                         stream: Optional[int] = None) -> None:
+    _check(_lib.bbp_accumulate_async(plan, formula, n, P, shard, nshards, d_slots, stream or None),
+           "bbp_accumulate_async")
+
+
+def bbp_finalize_async(plan: int, formula: int, n: int, P: int, d_slots: int, d_out: int, d_valid: int = 0,
+                       d_limbs: int = 0, stream: Optional[int] = None) -> None:
+    _check(_lib.bbp_finalize_async(plan, formula, n, P, d_slots, d_out, d_valid or None, d_limbs or None,
+                                   stream or None), "bbp_finalize_async")
 
 
 def bbp_plan_stats(plan: int) -> dict:

@@ -83,6 +83,19 @@ double head_term_imad(bool wide, int nb, int first, int lmax) {
   return wide ? 16.0 * sq + 5.0 * lmax + 8.0 : 4.0 * sq + 2.0 * lmax + 8.0;
 }
 
+void shard_range(const FormulaDef& f, uint32_t j, uint64_t n, uint32_t W, uint32_t shard, uint32_t nshards,
+                 uint64_t* k_begin, uint64_t* k_end) {
+  const uint64_t he = head_end(f, j, n - 1);
+  const uint64_t ne = natural_end(f, j, n - 1, W);
+  // he * shard / nshards without overflow: he < 2^60, nshards < 2^32
+  auto cut = [&](uint64_t i) -> uint64_t {
+    const unsigned __int128 v = static_cast<unsigned __int128>(he) * i / nshards;
+    return static_cast<uint64_t>(v);
+  };
+  *k_begin = cut(shard);
+  *k_end = shard + 1 == nshards ? ne : cut(shard + 1);
+}
+
 namespace {
 double range_imad(const FormulaDef& f, const SeriesDef& s, uint64_t d, uint32_t W, const TermRange& r, int lmax) {
   const int rb = r.wide ? 64 : 32;

@@ -56,6 +56,11 @@ void window_params(bool wide, int lbits, uint8_t* window, uint8_t* first);
 // quotient digit 5 or 2, plus 8 for the inverse.
 double head_term_imad(bool wide, int nb, int first, int lmax);
 
+// Shard `shard` of `nshards` of series j: the head [0, head_end) is cut evenly,
+// the tail [head_end, natural_end) belongs to the last shard.
+void shard_range(const FormulaDef& f, uint32_t j, uint64_t n, uint32_t W, uint32_t shard, uint32_t nshards,
+                 uint64_t* k_begin, uint64_t* k_end);
+
 // Appends the ranges of series j restricted to k in [k_lo, k_hi) (k_hi = UINT64_MAX:
 // natural end).  Returns 0, or -6 (modulus too large) / -1 (bad argument).
 int plan_series(const FormulaDef& f, uint32_t j, uint64_t n, uint32_t W, uint32_t lmax, uint64_t k_lo,

@@ -312,6 +312,52 @@ bbp_status bbp_bits_async(bbp_plan p, bbp_formula f, uint64_t n, uint32_t P, uin
   return BBP_OK;
 }
 
+bbp_status bbp_shard_range(bbp_formula f, uint32_t denominator, uint64_t n, uint32_t W, uint32_t shard,
+                           uint32_t nshards, uint64_t* k_begin, uint64_t* k_end) {
+  if (!valid_formula(f) || n == 0 || W == 0 || W % 32 != 0 || nshards == 0 || shard >= nshards) return BBP_EINVAL;
+  const FormulaDef& F = formula_def(f);
+  if (denominator >= F.count) return BBP_EINVAL;
+  uint64_t kb = 0, ke = 0;
+  shard_range(F, denominator, n, W, shard, nshards, &kb, &ke);
+  if (k_begin) *k_begin = kb;
+  if (k_end) *k_end = ke;
+  return BBP_OK;
+}
+
+bbp_status bbp_accumulate_async(bbp_plan p, bbp_formula f, uint64_t n, uint32_t P, uint32_t shard, uint32_t nshards,
+                                unsigned long long* d_slots, void* stream) {
+  if (!p || !valid_formula(f) || n == 0 || P == 0 || !d_slots || nshards == 0 || shard >= nshards)
+    return BBP_EINVAL;
+  uint32_t W;
+  if (!working_bits(P, p->guard, &W)) return BBP_EINVAL;
+  const FormulaDef& F = formula_def(f);
+  std::vector<TermRange> ranges;
+  for (uint32_t j = 0; j < F.count; ++j) {
+    uint64_t kb, ke;
+    shard_range(F, j, n, W, shard, nshards, &kb, &ke);
+    const bbp_status st = plan_query(f, n, W, static_cast<int>(j), kb, ke, ranges, nullptr);
+    if (st != BBP_OK) return st;
+  }
+  BBP_CUDA(cudaSetDevice(p->device));
+  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : p->stream;
+  p->stats = bbp_stats{};
+  return launch_ranges(p, f, n, W, ranges, d_slots, s);
+}
+
+bbp_status bbp_finalize_async(bbp_plan p, bbp_formula f, uint64_t n, uint32_t P, const unsigned long long* d_slots,
+                              uint8_t* d_out, uint32_t* d_valid, uint32_t* d_limbs, void* stream) {
+  if (!p || !valid_formula(f) || n == 0 || P == 0 || !d_slots || !d_out) return BBP_EINVAL;
+  uint32_t W;
+  if (!working_bits(P, p->guard, &W)) return BBP_EINVAL;
+  uint64_t N = 0;
+  const FormulaDef& F = formula_def(f);
+  for (uint32_t j = 0; j < F.count; ++j) N += natural_end(F, j, n - 1, W);
+  BBP_CUDA(cudaSetDevice(p->device));
+  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : p->stream;
+  BBP_CUDA(launch_finalize_bits(d_slots, static_cast<int>(W / 32), P, N + F.count + 1, d_out, d_valid, d_limbs, s));
+  return BBP_OK;
+}
+
 bbp_status bbp_bits_formula(bbp_plan p, bbp_formula f, uint64_t n, uint32_t P, uint8_t* out, uint32_t* valid_bits) {
   if (!p || !out) return BBP_EINVAL;
   bbp_status st = bbp_bits_async(p, f, n, P, p->d_bytes, p->d_valid, nullptr, p->stream);
