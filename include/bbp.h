@@ -47,7 +47,8 @@ typedef enum bbp_status {
   BBP_ETIMEOUT = -5,         /* a bounded device-side wait gave up */
   BBP_ERANGE = -6,           /* n so large that a modulus would reach 2^60 */
   BBP_EINVALID_BITS = -7,    /* strict mode: fewer than P bits certified */
-  BBP_ENOTFOUND = -8         /* unknown ticket */
+  BBP_ENOTFOUND = -8,        /* unknown ticket */
+  BBP_ESCRATCH = -9          /* bbp_partial_sum_noalloc: W beyond its fixed scratch (1280 bits) */
 } bbp_status;
 
 /* Eq. 2 (Bellard, 7 series, step 10, alternating) or Eq. 1 (BBP, 4 series, step 4). */
@@ -161,6 +162,31 @@ bbp_status bbp_plan_stats(bbp_plan p, bbp_stats* out);
  * 1: high half, 2: 32x32->64 wide, 3: 32-bit add).  Runs one CTA of 1024 threads
  * per SM and reports warp-lane operations per SM clock (median over SMs). */
 bbp_status bbp_imad_probe(bbp_plan p, int kind, double* lanes_per_clk_per_sm);
+
+/* No-allocation partial sum.  The paper has no counterpart: this entry point exists
+ * for callers that must not allocate device memory once running -- code whose GPU
+ * memory belongs to a pooling allocator it may not bypass, latency-bound loops that
+ * cannot afford the device-wide synchronization of cudaMalloc/cudaFree, or plugins
+ * with a fixed, preallocated budget.  Such callers cannot create a plan.
+ *
+ * Computes exactly what bbp_partial_sum_async computes for a plan with
+ * guard_bits = G (same arguments, W = roundup(P,32) + G), on the calling thread's
+ * current device, queued on `stream` (NULL: the legacy default stream); it does
+ * not wait.  d_out_limbs: caller-owned device memory for W/32 uint32 limbs.
+ * It calls no cudaMalloc, cudaFree or other allocating routine and needs no plan.
+ *
+ * Scratch: a fixed array of 40 uint64 carry-save accumulators (320 bytes) compiled
+ * into the library, held by every GPU that loads it until the process exits, so
+ * W is limited to 1280 bits: larger requests return BBP_ESCRATCH.  Every call on a
+ * device uses the same array and zeroes it first; calls that overlap on the GPU
+ * (other streams or threads) race on it and must be serialized by the caller.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress with that device current); make that first call before
+ * any stream capture.
+ * Errors: BBP_EINVAL as bbp_partial_sum, BBP_ERANGE, BBP_ESCRATCH, BBP_ECUDA. */
+bbp_status bbp_partial_sum_noalloc(bbp_formula f, uint32_t denominator, uint64_t k_begin, uint64_t k_end,
+                                   uint64_t n, uint32_t P, uint32_t guard_bits, uint32_t* d_out_limbs,
+                                   void* stream);
 
 #ifdef __cplusplus
 }

@@ -29,6 +29,7 @@ BBP_ETIMEOUT = -5
 BBP_ERANGE = -6
 BBP_EINVALID_BITS = -7
 BBP_ENOTFOUND = -8
+BBP_ESCRATCH = -9
 
 BBP_BELLARD = 0
 BBP_BBP = 1
@@ -99,6 +100,7 @@ def _load():
         "bbp_accumulate_async": ([vp, ctypes.c_int, u64, u32, u32, u32, vp, vp], ctypes.c_int),
         "bbp_finalize_async": ([vp, ctypes.c_int, u64, u32, vp, vp, vp, vp, vp], ctypes.c_int),
         "bbp_imad_probe": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "bbp_partial_sum_noalloc": ([ctypes.c_int, u32, u64, u64, u64, u32, u32, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -228,6 +230,18 @@ def bbp_imad_probe(plan: int, kind: int) -> float:
     v = ctypes.c_double()
     _check(_lib.bbp_imad_probe(plan, kind, ctypes.byref(v)), "bbp_imad_probe")
     return v.value
+
+
+def bbp_partial_sum_noalloc(formula: int, denominator: int, k_begin: int, k_end: Optional[int], n: int, P: int,
+                            guard_bits: int, d_out_limbs: int, stream: Optional[int] = None) -> None:
+    """Partial sum without a plan and without any allocation, for callers that may
+    not allocate device memory once running (pooled or fixed GPU memory budgets,
+    loops that cannot afford cudaMalloc's synchronization).  Writes W/32 limbs to
+    the caller's device buffer on the current device; asynchronous on `stream`.
+    Calls on one device share a fixed 320-byte scratch array, so overlapping calls
+    race; the first call on a device should come before any stream capture."""
+    _check(_lib.bbp_partial_sum_noalloc(formula, denominator, k_begin, UINT64_MAX if k_end is None else k_end,
+                                        n, P, guard_bits, d_out_limbs, stream or None), "bbp_partial_sum_noalloc")
 
 
 # ---------------------------------------------------------------- convenience wrapper

@@ -61,6 +61,7 @@ const char* bbp_status_str(bbp_status s) {
     case BBP_ERANGE: return "position out of range (modulus would reach 2^60)";
     case BBP_EINVALID_BITS: return "fewer bits certified than requested";
     case BBP_ENOTFOUND: return "unknown ticket";
+    case BBP_ESCRATCH: return "working precision exceeds the fixed scratch of the no-allocation entry point";
   }
   return "unknown status";
 }
