@@ -96,39 +96,78 @@ struct Mod64 {
 // block-local registers first and writes its outputs last, so the compiler may
 // place an output in the same register as any input (equal values are merged)
 // without changing the result.
+//
+// Multiply mix.  On GB300 the integer multiply pipe issues the low half of a
+// 32x32 product (mul.lo / mad.lo) at 64 lanes/clk/SM, the high half (mul.hi) at 30
+// and the full 64-bit product (mul.wide) at 25.  So a product whose two halves are
+// both needed is one mul.wide, a product of which only the high half is needed is
+// one mul.hi, and the low word of T + u m -- zero by the choice of u -- is never
+// formed: its carry is (T_0 != 0), taken on the ALU.
+//
+// SMALL: x1^2 < 2^32 (bitlen(m) <= 47, since x < 2m), so x1^2 needs no high half.
+template <bool SMALL>
 __device__ __forceinline__ void sqr_shift_redc64(uint32_t& x0, uint32_t& x1, uint32_t s, const Mod64& M,
                                                  bool do_shift) {
   uint32_t t0, t1, t2, t3;
   // T = x0^2 + (x0 * 2 x1) 2^32 + x1^2 2^64, with 2 x1 < 2^32 because x < 2^61
-  asm("{\n\t"
-      ".reg .u32 a0, a1, d1, s0, s1, s2, s3;\n\t"
-      "mov.u32        a0, %4;\n\t"
-      "mov.u32        a1, %5;\n\t"
-      "shl.b32        d1, a1, 1;\n\t"
-      "mul.lo.u32     s0, a0, a0;\n\t"
-      "mul.hi.u32     s1, a0, a0;\n\t"
-      "mul.lo.u32     s2, a1, a1;\n\t"
-      "mul.hi.u32     s3, a1, a1;\n\t"
-      "mad.lo.cc.u32  s1, a0, d1, s1;\n\t"
-      "madc.hi.cc.u32 s2, a0, d1, s2;\n\t"
-      "addc.u32       s3, s3, 0;\n\t"
-      "mov.u32        %0, s0;\n\t"
-      "mov.u32        %1, s1;\n\t"
-      "mov.u32        %2, s2;\n\t"
-      "mov.u32        %3, s3;\n\t"
-      "}"
-      : "=r"(t0), "=r"(t1), "=r"(t2), "=r"(t3)
-      : "r"(x0), "r"(x1));
+  if (SMALL) {
+    asm("{\n\t"
+        ".reg .u32 a0, a1, d1, s0, s1, s2, s3, q0, w0, w1;\n\t"
+        ".reg .u64 p00, p01;\n\t"
+        "mov.u32        a0, %4;\n\t"
+        "mov.u32        a1, %5;\n\t"
+        "shl.b32        d1, a1, 1;\n\t"
+        "mul.wide.u32   p00, a0, a0;\n\t"
+        "mul.wide.u32   p01, a0, d1;\n\t"
+        "mul.lo.u32     q0, a1, a1;\n\t"
+        "mov.b64        {s0, s1}, p00;\n\t"
+        "mov.b64        {w0, w1}, p01;\n\t"
+        "add.cc.u32     s1, s1, w0;\n\t"
+        "addc.cc.u32    s2, w1, q0;\n\t"
+        "addc.u32       s3, 0, 0;\n\t"
+        "mov.u32        %0, s0;\n\t"
+        "mov.u32        %1, s1;\n\t"
+        "mov.u32        %2, s2;\n\t"
+        "mov.u32        %3, s3;\n\t"
+        "}"
+        : "=r"(t0), "=r"(t1), "=r"(t2), "=r"(t3)
+        : "r"(x0), "r"(x1));
+  } else {
+    asm("{\n\t"
+        ".reg .u32 a0, a1, d1, s0, s1, s2, s3, w0, w1;\n\t"
+        ".reg .u64 p00, p01, p11;\n\t"
+        "mov.u32        a0, %4;\n\t"
+        "mov.u32        a1, %5;\n\t"
+        "shl.b32        d1, a1, 1;\n\t"
+        "mul.wide.u32   p00, a0, a0;\n\t"
+        "mul.wide.u32   p01, a0, d1;\n\t"
+        "mul.wide.u32   p11, a1, a1;\n\t"
+        "mov.b64        {s0, s1}, p00;\n\t"
+        "mov.b64        {w0, w1}, p01;\n\t"
+        "mov.b64        {s2, s3}, p11;\n\t"
+        "add.cc.u32     s1, s1, w0;\n\t"
+        "addc.cc.u32    s2, s2, w1;\n\t"
+        "addc.u32       s3, s3, 0;\n\t"
+        "mov.u32        %0, s0;\n\t"
+        "mov.u32        %1, s1;\n\t"
+        "mov.u32        %2, s2;\n\t"
+        "mov.u32        %3, s3;\n\t"
+        "}"
+        : "=r"(t0), "=r"(t1), "=r"(t2), "=r"(t3)
+        : "r"(x0), "r"(x1));
+  }
   if (do_shift) {  // window multiply by 2^s, s < 32
     t3 = __funnelshift_l(t2, t3, s);
     t2 = __funnelshift_l(t1, t2, s);
     t1 = __funnelshift_l(t0, t1, s);
     t0 <<= s;
   }
-  // two word-by-word Montgomery reduction steps: T <- (T + u m) / 2^32, twice
+  // two word-by-word Montgomery reduction steps: T <- (T + u m) / 2^32, twice.
+  // Per step: u = T_0 mp; (T + u m)/2^32 = (T >> 32) + hi(u m0) + (T_0 != 0) + u m1.
   uint32_t r0, r1;
   asm("{\n\t"
-      ".reg .u32 u, s0, s1, s2, s3, n0, n1, np;\n\t"
+      ".reg .u32 u, c, h, s0, s1, s2, s3, n0, n1, np;\n\t"
+      ".reg .u64 z, a, hz;\n\t"
       "mov.u32        s0, %2;\n\t"
       "mov.u32        s1, %3;\n\t"
       "mov.u32        s2, %4;\n\t"
@@ -136,20 +175,30 @@ __device__ __forceinline__ void sqr_shift_redc64(uint32_t& x0, uint32_t& x1, uin
       "mov.u32        n0, %6;\n\t"
       "mov.u32        n1, %7;\n\t"
       "mov.u32        np, %8;\n\t"
+      // step 1: word 0 vanishes; (s3 : s2 : s1) += hi(u m0) + c + u m1
       "mul.lo.u32     u, s0, np;\n\t"
-      "mad.lo.cc.u32  s0, u, n0, s0;\n\t"
-      "madc.hi.cc.u32 s1, u, n0, s1;\n\t"
-      "madc.hi.cc.u32 s2, u, n1, s2;\n\t"
+      "min.u32        c, s0, 1;\n\t"
+      "mul.hi.u32     h, u, n0;\n\t"
+      "mul.wide.u32   z, u, n1;\n\t"
+      "add.u32        h, h, c;\n\t"
+      "mov.b64        a, {s1, s2};\n\t"
+      "add.cc.u64     a, a, z;\n\t"
       "addc.u32       s3, s3, 0;\n\t"
-      "mad.lo.cc.u32  s1, u, n1, s1;\n\t"
-      "addc.cc.u32    s2, s2, 0;\n\t"
+      "cvt.u64.u32    hz, h;\n\t"
+      "add.cc.u64     a, a, hz;\n\t"
       "addc.u32       s3, s3, 0;\n\t"
+      "mov.b64        {s1, s2}, a;\n\t"
+      // step 2: word 1 vanishes; the result (s3 : s2) + hi(u m0) + c + u m1 < 2m fits 64 bits
       "mul.lo.u32     u, s1, np;\n\t"
-      "mad.lo.cc.u32  s1, u, n0, s1;\n\t"
-      "madc.hi.cc.u32 s2, u, n0, s2;\n\t"
-      "madc.hi.u32    s3, u, n1, s3;\n\t"
-      "mad.lo.cc.u32  s2, u, n1, s2;\n\t"
-      "addc.u32       s3, s3, 0;\n\t"
+      "min.u32        c, s1, 1;\n\t"
+      "mul.hi.u32     h, u, n0;\n\t"
+      "mul.wide.u32   z, u, n1;\n\t"
+      "add.u32        h, h, c;\n\t"
+      "mov.b64        a, {s2, s3};\n\t"
+      "add.u64        a, a, z;\n\t"
+      "cvt.u64.u32    hz, h;\n\t"
+      "add.u64        a, a, hz;\n\t"
+      "mov.b64        {s2, s3}, a;\n\t"
       "mov.u32        %0, s2;\n\t"
       "mov.u32        %1, s3;\n\t"
       "}"
@@ -181,23 +230,28 @@ __device__ __forceinline__ void reduce_once64(uint32_t& x0, uint32_t& x1, const 
 }
 
 // One exact-division digit: for x < m returns u = x * (-m^-1) mod 2^32 and
-// replaces x by (x + u m) / 2^32 (still < m).  The low word of x + u m is 0 by the
-// choice of u, so only its carry matters.
+// replaces x by (x + u m) / 2^32 = x1 + hi(u m0) + (x0 != 0) + u m1 (still < m).
+// The low word of x + u m is 0 by the choice of u, so only its carry matters.
 __device__ __forceinline__ uint32_t hensel_step64(uint32_t& x0, uint32_t& x1, const Mod64& M) {
   uint32_t u, y0, y1;
   asm("{\n\t"
-      ".reg .u32 q, a0, a1, n0, n1, np;\n\t"
+      ".reg .u32 q, c, h, a0, a1, n0, n1, np;\n\t"
+      ".reg .u64 z, r, w;\n\t"
       "mov.u32        a0, %3;\n\t"
       "mov.u32        a1, %4;\n\t"
       "mov.u32        n0, %5;\n\t"
       "mov.u32        n1, %6;\n\t"
       "mov.u32        np, %7;\n\t"
       "mul.lo.u32     q, a0, np;\n\t"
-      "mad.lo.cc.u32  a0, q, n0, a0;\n\t"
-      "madc.hi.cc.u32 a0, q, n0, a1;\n\t"
-      "madc.hi.u32    a1, q, n1, 0;\n\t"
-      "mad.lo.cc.u32  a0, q, n1, a0;\n\t"
-      "addc.u32       a1, a1, 0;\n\t"
+      "min.u32        c, a0, 1;\n\t"
+      "mul.hi.u32     h, q, n0;\n\t"
+      "mul.wide.u32   z, q, n1;\n\t"
+      "add.u32        h, h, c;\n\t"
+      "cvt.u64.u32    r, h;\n\t"
+      "add.u64        r, r, z;\n\t"
+      "cvt.u64.u32    w, a1;\n\t"
+      "add.u64        r, r, w;\n\t"
+      "mov.b64        {a0, a1}, r;\n\t"
       "mov.u32        %0, q;\n\t"
       "mov.u32        %1, a0;\n\t"
       "mov.u32        %2, a1;\n\t"
@@ -225,12 +279,10 @@ struct Mod32 {
 };
 
 __device__ __forceinline__ uint32_t sqr_shift_redc32(uint32_t x, uint32_t s, const Mod32& M, bool do_shift) {
-  uint32_t t0 = x * x;
-  uint32_t t1 = __umulhi(x, x);
-  if (do_shift) {
-    t1 = __funnelshift_l(t0, t1, s);
-    t0 <<= s;
-  }
+  uint64_t T = static_cast<uint64_t>(x) * x;  // one 32x32->64 product
+  if (do_shift) T <<= s;
+  const uint32_t t0 = lo32(T);
+  const uint32_t t1 = hi32(T);
   const uint32_t u = t0 * M.mp;
   // t0 + lo(u m) = 0 (mod 2^32): the carry out of that word is (t0 != 0)
   return t1 + __umulhi(u, M.m) + (t0 != 0u ? 1u : 0u);

@@ -18,13 +18,64 @@ namespace {
 // ---------------------------------------------------------------- head terms
 //
 // Work split: a warp owns a tile of 32 * S * run consecutive terms; lane l, stream s
-// owns the run starting at tile + (l S + s) run.  Runs keep R mod m incremental and
-// keep the exponents of a warp within 10 * 32 * S * run of each other, so the
-// ladder length (warp maximum of the exponent bit length) is almost always shared.
-// Each stream evaluates a pair (k, k+1) per step, so (-1)^k is static in the code.
-template <int LMAX, bool WIDE, int S>
+// owns the run starting at tile + (l S + s) run.  Along a run, m, the exponent and
+// R mod m advance incrementally, and the exponents of a warp stay within
+// step * 32 * S * run of each other, so the ladder length (the warp maximum of the
+// exponent bit length) is almost always shared.  Each stream evaluates a pair
+// (k, k+1) per step, so (-1)^k is static in the code.
+
+// State of one stream at its current term.
+struct StreamState {
+  uint64_t rel;  // term index relative to k_begin (clamped to the last term)
+  uint64_t m;    // modulus a k + b
+  uint64_t E;    // exponent of the residue the ladder produces: e + W = d + c - step k + W
+  RTrack tr;     // R = q m + r
+};
+
+template <bool WIDE, bool SMALL, int NT>
+__device__ __forceinline__ void square_all(uint32_t (&x0)[NT], uint32_t (&x1)[NT], const uint32_t (&m0)[NT],
+                                           const uint32_t (&m1)[NT], const uint32_t (&mp)[NT],
+                                           const uint32_t (&sh)[NT], bool do_shift) {
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    if (WIDE) sqr_shift_redc64<SMALL>(x0[t], x1[t], sh[t], Mod64{m0[t], m1[t], mp[t]}, do_shift);
+    else x0[t] = sqr_shift_redc32(x0[t], sh[t], Mod32{m0[t], mp[t]}, do_shift);
+  }
+}
+
+// Quotient digits of every term, least significant first, folded straight into
+// the LMAX-limb sum with a signed carry (odd terms subtracted when NEG_ODD).
+template <bool WIDE, bool NEG_ODD, int NT, int LMAX>
+__device__ __forceinline__ void fold_digits(uint32_t (&acc)[LMAX], uint32_t (&x0)[NT], uint32_t (&x1)[NT],
+                                            const uint32_t (&m0)[NT], const uint32_t (&m1)[NT],
+                                            const uint32_t (&mp)[NT], const uint32_t (&vmask)[NT]) {
+  int64_t carry = 0;
+#pragma unroll
+  for (int i = 0; i < LMAX; ++i) {
+    int64_t sum = static_cast<int64_t>(acc[i]) + carry;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      uint32_t q;
+      if (WIDE) {
+        q = hensel_step64(x0[t], x1[t], Mod64{m0[t], m1[t], mp[t]});
+      } else {
+        q = x0[t] * mp[t];
+        x0[t] = __umulhi(q, m0[t]) + (x0[t] != 0u ? 1u : 0u);
+      }
+      q &= vmask[t];
+      if (NEG_ODD && (t & 1)) sum -= q;
+      else sum += q;
+    }
+    acc[i] = static_cast<uint32_t>(sum);
+    carry = sum >> 32;
+  }
+}
+
+template <int LMAX, int PATH, int S>
 __global__ void __launch_bounds__(kHeadThreads) head_kernel(const HeadArgs A, const uint64_t ntiles) {
   constexpr int NT = 2 * S;
+  constexpr bool WIDE = PATH > 0;         // 64-bit moduli (PATH 1: bitlen(m) <= 47, PATH 2: <= 60)
+  constexpr bool SMALL = PATH == 1;
   constexpr int RB = WIDE ? 64 : 32;
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t wid = threadIdx.x >> 5;
@@ -33,26 +84,29 @@ __global__ void __launch_bounds__(kHeadThreads) head_kernel(const HeadArgs A, co
   const uint64_t run = A.run;
   const uint64_t tile = 32ull * S * run;
   const uint64_t last = A.count - 1;
-  const uint32_t window = A.window;
-  const uint32_t wmask = (1u << window) - 1u;
+  const int window = static_cast<int>(A.window);
+  // exponent of the first term: E(k) = e0 - step k
+  const uint64_t e0 = A.d + static_cast<int64_t>(A.c) + A.W;
 
   uint32_t acc[LMAX];
 #pragma unroll
   for (int i = 0; i < LMAX; ++i) acc[i] = 0;
 
   for (uint64_t ti = warp; ti < ntiles; ti += nwarps) {
-    uint64_t base[S], kcur[S];
-    RTrack tr[S];
+    uint64_t base[S];
+    StreamState st[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       base[s] = ti * tile + (static_cast<uint64_t>(lane) * S + s) * run;
-      kcur[s] = A.k_begin + min(base[s], last);
-      tr[s] = r_mod_m_bitserial<RB>(static_cast<uint64_t>(A.a) * kcur[s] + A.b);
+      st[s].rel = min(base[s], last);
+      const uint64_t k = A.k_begin + st[s].rel;
+      st[s].m = static_cast<uint64_t>(A.a) * k + A.b;
+      st[s].E = e0 - static_cast<uint64_t>(A.step) * k;
+      st[s].tr = r_mod_m_bitserial<RB>(st[s].m);
     }
     for (uint32_t i = 0; i < run; i += 2) {
       uint64_t v[NT];
-      uint32_t x0[NT], x1[NT], m0[NT], m1[NT], mp[NT];
-      bool valid[NT];
+      uint32_t x0[NT], x1[NT], m0[NT], m1[NT], mp[NT], vmask[NT];
       int nbl = 0;
 #pragma unroll
       for (int s = 0; s < S; ++s) {
@@ -60,21 +114,20 @@ __global__ void __launch_bounds__(kHeadThreads) head_kernel(const HeadArgs A, co
         for (int p = 0; p < 2; ++p) {
           const int t = 2 * s + p;
           const uint64_t rel = base[s] + i + p;
-          valid[t] = rel < A.count;
-          const uint64_t k = A.k_begin + min(rel, last);
-          const uint64_t m = static_cast<uint64_t>(A.a) * k + A.b;
-          if (k != kcur[s]) {
-            r_mod_m_advance<RB>(tr[s], m, A.a);
-            kcur[s] = k;
+          const bool valid = rel < A.count;
+          if (valid && rel != st[s].rel) {  // the next k of the run: advance by one
+            st[s].rel = rel;
+            st[s].m += A.a;
+            st[s].E -= A.step;
+            r_mod_m_advance<RB>(st[s].tr, st[s].m, A.a);
           }
-          x0[t] = lo32(tr[s].r);
-          x1[t] = hi32(tr[s].r);
-          m0[t] = lo32(m);
-          m1[t] = hi32(m);
+          x0[t] = lo32(st[s].tr.r);
+          x1[t] = hi32(st[s].tr.r);
+          m0[t] = lo32(st[s].m);
+          m1[t] = hi32(st[s].m);
           mp[t] = neg_inverse32(m0[t]);
-          // E = d + c - step k + W >= W >= RB for head terms; v = E - RB
-          const uint64_t E = A.d + static_cast<int64_t>(A.c) - static_cast<uint64_t>(A.step) * k + A.W;
-          v[t] = E - RB;
+          vmask[t] = valid ? 0xffffffffu : 0u;
+          v[t] = st[s].E - RB;  // E >= W >= RB for head terms
           nbl = max(nbl, bitlen64(v[t]));
         }
       }
@@ -95,53 +148,35 @@ __global__ void __launch_bounds__(kHeadThreads) head_kernel(const HeadArgs A, co
         }
         rem[t] = low > 0 ? (v[t] & ((1ull << low) - 1ull)) : 0ull;
       }
-      // remaining bits, top down, in groups of `window` bits aligned from the top;
-      // the group's value is multiplied in (a shift) with its last squaring.
-      int cnt = static_cast<int>(window);
-      for (int p = low - 1; p >= 0; --p) {
-        --cnt;
-        if (p == 0) {
-          const uint32_t gm = (1u << (window - static_cast<uint32_t>(cnt))) - 1u;
-#pragma unroll
-          for (int t = 0; t < NT; ++t) {
-            const uint32_t sh = static_cast<uint32_t>(rem[t]) & gm;
-            if (WIDE) sqr_shift_redc64(x0[t], x1[t], sh, Mod64{m0[t], m1[t], mp[t]}, true);
-            else x0[t] = sqr_shift_redc32(x0[t], sh, Mod32{m0[t], mp[t]}, true);
-          }
-        } else if (cnt == 0) {
-#pragma unroll
-          for (int t = 0; t < NT; ++t) {
-            const uint32_t sh = static_cast<uint32_t>(rem[t] >> p) & wmask;
-            if (WIDE) sqr_shift_redc64(x0[t], x1[t], sh, Mod64{m0[t], m1[t], mp[t]}, true);
-            else x0[t] = sqr_shift_redc32(x0[t], sh, Mod32{m0[t], mp[t]}, true);
-          }
-          cnt = static_cast<int>(window);
-        } else {
-#pragma unroll
-          for (int t = 0; t < NT; ++t) {
-            if (WIDE) sqr_shift_redc64(x0[t], x1[t], 0u, Mod64{m0[t], m1[t], mp[t]}, false);
-            else x0[t] = sqr_shift_redc32(x0[t], 0u, Mod32{m0[t], mp[t]}, false);
-          }
+      // remaining bits, top down, in groups of `window` bits aligned from the top:
+      // len - 1 plain squarings, then one squaring with the group's value shifted in
+      const uint32_t zero[NT] = {};
+      int p = low;
+      while (p > 0) {
+        const int len = min(window, p);
+        p -= len;
+        switch (len) {
+          case 4: square_all<WIDE, SMALL, NT>(x0, x1, m0, m1, mp, zero, false);  // fall through
+          case 3: square_all<WIDE, SMALL, NT>(x0, x1, m0, m1, mp, zero, false);  // fall through
+          case 2: square_all<WIDE, SMALL, NT>(x0, x1, m0, m1, mp, zero, false);  // fall through
+          default: break;
         }
+        uint32_t sh[NT];
+#pragma unroll
+        for (int t = 0; t < NT; ++t) sh[t] = static_cast<uint32_t>(rem[t] >> p) & ((1u << len) - 1u);
+        square_all<WIDE, SMALL, NT>(x0, x1, m0, m1, mp, sh, true);
       }
-      // s = 2^E mod m, then the W-bit quotient digits, then the signed sum
+      // s = 2^E mod m, then the W-bit quotient digits folded into the signed sum
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
-        uint32_t q[LMAX];
         if (WIDE) {
-          Mod64 M{m0[t], m1[t], mp[t]};
-          reduce_once64(x0[t], x1[t], M);
-          hensel_digits64<LMAX>(x0[t], x1[t], M, q);
-        } else {
-          Mod32 M{m0[t], mp[t]};
-          const uint32_t x = x0[t] >= m0[t] ? x0[t] - m0[t] : x0[t];
-          hensel_digits32<LMAX>(x, M, q);
-        }
-        if (valid[t]) {
-          if ((t & 1) && A.alternating) sub_limbs<LMAX>(acc, q);
-          else add_limbs<LMAX>(acc, q);
+          reduce_once64(x0[t], x1[t], Mod64{m0[t], m1[t], mp[t]});
+        } else if (x0[t] >= m0[t]) {
+          x0[t] -= m0[t];
         }
       }
+      if (A.alternating) fold_digits<WIDE, true, NT, LMAX>(acc, x0, x1, m0, m1, mp, vmask);
+      else fold_digits<WIDE, false, NT, LMAX>(acc, x0, x1, m0, m1, mp, vmask);
     }
   }
 
@@ -360,43 +395,55 @@ __global__ void imad_probe_kernel(int iters, unsigned long long* cycles, uint32_
 namespace {
 constexpr int kLmaxList[] = {3, 4, 6, 10, 16, 40};
 
-template <int LMAX, bool WIDE, int S>
+template <int LMAX, int PATH, int S>
 cudaError_t launch_head_t(const HeadArgs& a, int blocks, cudaStream_t s) {
   const uint64_t tile = 32ull * S * a.run;
   const uint64_t ntiles = (a.count + tile - 1) / tile;
-  head_kernel<LMAX, WIDE, S><<<blocks, kHeadThreads, 0, s>>>(a, ntiles);
+  head_kernel<LMAX, PATH, S><<<blocks, kHeadThreads, 0, s>>>(a, ntiles);
   return cudaGetLastError();
 }
 
-template <int LMAX, bool WIDE, int S>
+template <int LMAX, int PATH, int S>
 int occupancy_t() {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, head_kernel<LMAX, WIDE, S>, kHeadThreads, 0) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, head_kernel<LMAX, PATH, S>, kHeadThreads, 0) != cudaSuccess)
     return 1;
   return n > 0 ? n : 1;
 }
 
-template <int LMAX>
-int occupancy_l(int wide, int streams) {
-  if (wide) return streams == 2 ? occupancy_t<LMAX, true, 2>() : occupancy_t<LMAX, true, 1>();
-  return streams == 2 ? occupancy_t<LMAX, false, 2>() : occupancy_t<LMAX, false, 1>();
+template <int LMAX, int PATH>
+int occupancy_p(int streams) {
+  return streams == 2 ? occupancy_t<LMAX, PATH, 2>() : occupancy_t<LMAX, PATH, 1>();
 }
 
 template <int LMAX>
-cudaError_t launch_head_l(const HeadArgs& a, int wide, int streams, int blocks, cudaStream_t s) {
-  if (wide) return streams == 2 ? launch_head_t<LMAX, true, 2>(a, blocks, s) : launch_head_t<LMAX, true, 1>(a, blocks, s);
-  return streams == 2 ? launch_head_t<LMAX, false, 2>(a, blocks, s) : launch_head_t<LMAX, false, 1>(a, blocks, s);
+int occupancy_l(int path, int streams) {
+  if (path == 2) return occupancy_p<LMAX, 2>(streams);
+  if (path == 1) return occupancy_p<LMAX, 1>(streams);
+  return occupancy_p<LMAX, 0>(streams);
+}
+
+template <int LMAX, int PATH>
+cudaError_t launch_head_p(const HeadArgs& a, int streams, int blocks, cudaStream_t s) {
+  return streams == 2 ? launch_head_t<LMAX, PATH, 2>(a, blocks, s) : launch_head_t<LMAX, PATH, 1>(a, blocks, s);
+}
+
+template <int LMAX>
+cudaError_t launch_head_l(const HeadArgs& a, int path, int streams, int blocks, cudaStream_t s) {
+  if (path == 2) return launch_head_p<LMAX, 2>(a, streams, blocks, s);
+  if (path == 1) return launch_head_p<LMAX, 1>(a, streams, blocks, s);
+  return launch_head_p<LMAX, 0>(a, streams, blocks, s);
 }
 }  // namespace
 
-int head_occupancy(int wide, int streams, int lmax) {
+int head_occupancy(int path, int streams, int lmax) {
   switch (lmax) {
-    case 3: return occupancy_l<3>(wide, streams);
-    case 4: return occupancy_l<4>(wide, streams);
-    case 6: return occupancy_l<6>(wide, streams);
-    case 10: return occupancy_l<10>(wide, streams);
-    case 16: return occupancy_l<16>(wide, streams);
-    case 40: return occupancy_l<40>(wide, streams);
+    case 3: return occupancy_l<3>(path, streams);
+    case 4: return occupancy_l<4>(path, streams);
+    case 6: return occupancy_l<6>(path, streams);
+    case 10: return occupancy_l<10>(path, streams);
+    case 16: return occupancy_l<16>(path, streams);
+    case 40: return occupancy_l<40>(path, streams);
     default: return 1;
   }
 }
@@ -407,14 +454,14 @@ int head_lmax_for(int L) {
   return 0;
 }
 
-cudaError_t launch_head(const HeadArgs& a, int wide, int streams, int lmax, int blocks, cudaStream_t s) {
+cudaError_t launch_head(const HeadArgs& a, int path, int streams, int lmax, int blocks, cudaStream_t s) {
   switch (lmax) {
-    case 3: return launch_head_l<3>(a, wide, streams, blocks, s);
-    case 4: return launch_head_l<4>(a, wide, streams, blocks, s);
-    case 6: return launch_head_l<6>(a, wide, streams, blocks, s);
-    case 10: return launch_head_l<10>(a, wide, streams, blocks, s);
-    case 16: return launch_head_l<16>(a, wide, streams, blocks, s);
-    case 40: return launch_head_l<40>(a, wide, streams, blocks, s);
+    case 3: return launch_head_l<3>(a, path, streams, blocks, s);
+    case 4: return launch_head_l<4>(a, path, streams, blocks, s);
+    case 6: return launch_head_l<6>(a, path, streams, blocks, s);
+    case 10: return launch_head_l<10>(a, path, streams, blocks, s);
+    case 16: return launch_head_l<16>(a, path, streams, blocks, s);
+    case 40: return launch_head_l<40>(a, path, streams, blocks, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -44,15 +44,16 @@ constexpr int kMaxLimbs = 40;    // W <= 1280 bits
 constexpr int kHeadThreads = 256;
 
 // Launch helpers (defined in bbp_kernels.cu).  They return cudaGetLastError().
-// variant: 0 = 32-bit modulus path (m < 2^29), 1 = 64-bit path (m < 2^60).
-cudaError_t launch_head(const HeadArgs& a, int wide, int streams, int lmax, int blocks, cudaStream_t s);
+// path: 0 = 32-bit moduli (bitlen <= 29), 1 = 64-bit moduli with bitlen <= 47,
+//       2 = 64-bit moduli with bitlen <= 60.
+cudaError_t launch_head(const HeadArgs& a, int path, int streams, int lmax, int blocks, cudaStream_t s);
 cudaError_t launch_tail(const TailArgs& a, cudaStream_t s);
 cudaError_t launch_zero_slots(unsigned long long* slots, int L, cudaStream_t s);
 cudaError_t launch_fold_limbs(const unsigned long long* slots, int L, uint32_t* out_limbs, cudaStream_t s);
 cudaError_t launch_finalize_bits(const unsigned long long* slots, int L, uint32_t P, uint64_t bound,
                                  uint8_t* out_bytes, uint32_t* valid_bits, uint32_t* out_limbs, cudaStream_t s);
 int head_lmax_for(int L);  // smallest compiled limb capacity >= L, or 0
-int head_occupancy(int wide, int streams, int lmax);  // resident CTAs per SM of that instantiation
+int head_occupancy(int path, int streams, int lmax);  // resident CTAs per SM of that instantiation
 cudaError_t launch_imad_probe(int kind, int blocks, int threads, int iters, unsigned long long* cycles_out,
                               uint32_t* smid_out, uint32_t* sink, cudaStream_t s);
 

@@ -104,10 +104,10 @@ extern "C" bbp_status bbp_partial_sum_noalloc(bbp_formula f, uint32_t denominato
     for (int part = 0; part < 2; ++part) {
       const uint64_t kb = cuts[part], ke = cuts[part + 1];
       if (kb >= ke) continue;
-      const int wide = part;
       const int lbits = bitlen(static_cast<uint64_t>(s.a) * (ke - 1) + s.b);
+      const int path = part == 0 ? 0 : path_for_bits(lbits);
       uint8_t window, first;
-      window_params(wide != 0, lbits, &window, &first);
+      window_params(path, lbits, &window, &first);
       HeadArgs a{};
       a.d = d;
       a.k_begin = kb;
@@ -127,9 +127,9 @@ extern "C" bbp_status bbp_partial_sum_noalloc(bbp_formula f, uint32_t denominato
       const uint64_t tile = 32ull * kRun;
       const uint64_t ntiles = (a.count + tile - 1) / tile;
       const uint64_t want = (ntiles + kHeadThreads / 32 - 1) / (kHeadThreads / 32);
-      const uint64_t cap = static_cast<uint64_t>(head_occupancy(wide, 1, lmax)) * static_cast<uint64_t>(sms);
+      const uint64_t cap = static_cast<uint64_t>(head_occupancy(path, 1, lmax)) * static_cast<uint64_t>(sms);
       const int blocks = static_cast<int>(std::max<uint64_t>(1, std::min(want, cap)));
-      if (launch_head(a, wide, 1, lmax, blocks, st) != cudaSuccess) return BBP_ECUDA;
+      if (launch_head(a, path, 1, lmax, blocks, st) != cudaSuccess) return BBP_ECUDA;
     }
   }
   // tail terms

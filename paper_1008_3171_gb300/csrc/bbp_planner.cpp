@@ -64,23 +64,30 @@ uint64_t natural_end(const FormulaDef& f, uint32_t j, uint64_t d, uint32_t W) {
   }
 }
 
-void window_params(bool wide, int lbits, uint8_t* window, uint8_t* first) {
+void window_params(int path, int lbits, uint8_t* window, uint8_t* first) {
   // shifted reduction keeps x < 2m while lbits + s <= 61 (64-bit) / <= 30 (32-bit);
-  // the first window (x = (R mod m) << w0) needs lbits + 2 w0 + 1 <= 64 / 32.
+  // the first window (x = (R mod m) << w0) needs lbits + 2 w0 + 1 <= 64 / 32, and on
+  // path 1 also x < 2^48 (x1^2 < 2^32), i.e. lbits + w0 <= 48.
+  const bool wide = path > 0;
   const int shift_cap = wide ? 61 - lbits : 30 - lbits;
   const int rbits = wide ? 64 : 32;
   int w = 0;
   while (w < 4 && (1 << (w + 1)) - 1 <= shift_cap) ++w;
   int h = 0;
-  while (h < 4 && lbits + 2 * ((1 << (h + 1)) - 1) + 1 <= rbits) ++h;
+  while (h < 4 && lbits + 2 * ((1 << (h + 1)) - 1) + 1 <= rbits &&
+         (path != 1 || lbits + (1 << (h + 1)) - 1 <= 48))
+    ++h;
   *window = static_cast<uint8_t>(w);
   *first = static_cast<uint8_t>(h);
 }
 
-double head_term_imad(bool wide, int nb, int first, int lmax) {
+int path_for_bits(int lbits) { return lbits < kWideMinBits ? 0 : (lbits <= kSmallMaxBits ? 1 : 2); }
+
+double head_term_imad(int path, int nb, int first, int lmax) {
   const int h = nb > 0 ? std::min(first, nb - 1) : 0;
   const int sq = nb - h;
-  return wide ? 16.0 * sq + 5.0 * lmax + 8.0 : 4.0 * sq + 2.0 * lmax + 8.0;
+  if (path == 0) return 4.0 * sq + 2.0 * lmax + 8.0;
+  return (path == 1 ? 13.0 : 14.0) * sq + 4.0 * lmax + 8.0;
 }
 
 void shard_range(const FormulaDef& f, uint32_t j, uint64_t n, uint32_t W, uint32_t shard, uint32_t nshards,
@@ -98,7 +105,7 @@ void shard_range(const FormulaDef& f, uint32_t j, uint64_t n, uint32_t W, uint32
 
 namespace {
 double range_imad(const FormulaDef& f, const SeriesDef& s, uint64_t d, uint32_t W, const TermRange& r, int lmax) {
-  const int rb = r.wide ? 64 : 32;
+  const int rb = r.path ? 64 : 32;
   const int64_t v0 = static_cast<int64_t>(d) + s.c + static_cast<int64_t>(W) - rb;  // v at k = 0
   const int64_t k_lo = static_cast<int64_t>(r.k_begin);
   const int64_t k_hi = static_cast<int64_t>(r.k_begin + r.count) - 1;
@@ -109,7 +116,7 @@ double range_imad(const FormulaDef& f, const SeriesDef& s, uint64_t d, uint32_t 
     // lo_v <= v0 - step k <= hi_v
     const int64_t ka = std::max(k_lo, ceil_div(v0 - hi_v, f.step));
     const int64_t kb = std::min(k_hi, floor_div(v0 - lo_v, f.step));
-    if (kb >= ka) total += static_cast<double>(kb - ka + 1) * head_term_imad(r.wide, i, r.first, lmax);
+    if (kb >= ka) total += static_cast<double>(kb - ka + 1) * head_term_imad(r.path, i, r.first, lmax);
   }
   return total;
 }
@@ -130,7 +137,7 @@ int plan_series(const FormulaDef& f, uint32_t j, uint64_t n, uint32_t W, uint32_
   const uint64_t head_lo = std::max(k_lo, s.b == 1 ? uint64_t{1} : uint64_t{0});
   const uint64_t head_hi = std::min(hi, he);
   if (head_lo < head_hi) {
-    struct Group { uint64_t k0, k1; int lmax_bits; bool wide; uint8_t w, h; };
+    struct Group { uint64_t k0, k1; int lmax_bits; int path; uint8_t w, h; };
     std::vector<Group> groups;
     const int l_first = bitlen(static_cast<uint64_t>(s.a) * head_lo + s.b);
     const int l_last = bitlen(static_cast<uint64_t>(s.a) * (head_hi - 1) + s.b);
@@ -138,15 +145,15 @@ int plan_series(const FormulaDef& f, uint32_t j, uint64_t n, uint32_t W, uint32_
       uint64_t k0 = std::max(head_lo, first_k_at_least(1ull << (l - 1), s.a, s.b));
       uint64_t k1 = std::min(head_hi, first_k_at_least(1ull << l, s.a, s.b));
       if (k0 >= k1) continue;
-      const bool wide = l >= kWideMinBits;
+      const int path = path_for_bits(l);
       uint8_t w, h;
-      window_params(wide, l, &w, &h);
-      if (!groups.empty() && groups.back().wide == wide && groups.back().w == w && groups.back().h == h &&
+      window_params(path, l, &w, &h);
+      if (!groups.empty() && groups.back().path == path && groups.back().w == w && groups.back().h == h &&
           groups.back().k1 == k0) {
         groups.back().k1 = k1;
         groups.back().lmax_bits = l;
       } else {
-        groups.push_back(Group{k0, k1, l, wide, w, h});
+        groups.push_back(Group{k0, k1, l, path, w, h});
       }
     }
     // fold small groups into their larger-modulus neighbour (whose parameters are
@@ -154,14 +161,14 @@ int plan_series(const FormulaDef& f, uint32_t j, uint64_t n, uint32_t W, uint32_
     std::vector<Group> merged;
     for (size_t i = 0; i < groups.size(); ++i) {
       Group g = groups[i];
-      while (g.k1 - g.k0 < kMinRangeTerms && i + 1 < groups.size() && groups[i + 1].wide == g.wide) {
+      while (g.k1 - g.k0 < kMinRangeTerms && i + 1 < groups.size() && groups[i + 1].path == g.path) {
         const Group& nx = groups[++i];
         g.k1 = nx.k1;
         g.lmax_bits = nx.lmax_bits;
         g.w = nx.w;
         g.h = nx.h;
       }
-      if (!merged.empty() && g.k1 - g.k0 < kMinRangeTerms && merged.back().wide == g.wide) {
+      if (!merged.empty() && g.k1 - g.k0 < kMinRangeTerms && merged.back().path == g.path) {
         merged.back().k1 = g.k1;
         merged.back().lmax_bits = g.lmax_bits;
         merged.back().w = g.w;
@@ -174,7 +181,7 @@ int plan_series(const FormulaDef& f, uint32_t j, uint64_t n, uint32_t W, uint32_
       TermRange r{};
       r.j = j;
       r.tail = 0;
-      r.wide = g.wide ? 1 : 0;
+      r.path = static_cast<uint8_t>(g.path);
       r.window = g.w;
       r.first = g.h;
       r.k_begin = g.k0;

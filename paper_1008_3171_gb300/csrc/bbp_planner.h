@@ -24,14 +24,15 @@ struct FormulaDef {
 const FormulaDef& formula_def(int f);
 
 constexpr uint32_t kMaxWorkingBits = 1280;   // 40 limbs
-constexpr int kWideMinBits = 30;             // moduli with bitlen >= 30 take the 64-bit path
+constexpr int kWideMinBits = 30;             // moduli with bitlen >= 30 take a 64-bit path
+constexpr int kSmallMaxBits = 47;            // 64-bit path 1 (x1^2 < 2^32) up to this bitlen
 constexpr int kMaxModulusBits = 60;          // 64-bit path bound
 
 // A contiguous run of terms of one series with one kernel configuration.
 struct TermRange {
   uint32_t j;         // series index
   uint8_t tail;       // 0 head (e >= 0), 1 tail (e < 0)
-  uint8_t wide;       // head: 64-bit modulus path
+  uint8_t path;       // head: 0 32-bit moduli, 1 64-bit (bitlen <= 47), 2 64-bit
   uint8_t window;     // head: ladder window bits
   uint8_t first;      // head: first-window bits
   uint64_t k_begin;   // first k
@@ -48,13 +49,20 @@ bool working_bits(uint32_t P, uint32_t G, uint32_t* W);
 uint64_t head_end(const FormulaDef& f, uint32_t j, uint64_t d);
 uint64_t natural_end(const FormulaDef& f, uint32_t j, uint64_t d, uint32_t W);
 
-// Ladder parameters for moduli of at most `lbits` bits on the given path.
-void window_params(bool wide, int lbits, uint8_t* window, uint8_t* first);
+// Kernel path for moduli of `lbits` bits.
+int path_for_bits(int lbits);
 
-// Modelled 32-bit multiply instructions of one head term whose ladder exponent
-// has nb bits (see the kernel): per squaring 16 (64-bit) or 4 (32-bit), per
-// quotient digit 5 or 2, plus 8 for the inverse.
-double head_term_imad(bool wide, int nb, int first, int lmax);
+// Ladder parameters for moduli of at most `lbits` bits on the given path.
+void window_params(int path, int lbits, uint8_t* window, uint8_t* first);
+
+// Algorithmic work of one head term whose ladder exponent has nb bits, counted as
+// 32-bit halves of 32x32-bit products (the low or high word of a product; a full
+// 64-bit product counts 2).  64-bit moduli: per Montgomery squaring 5 (x0^2 and
+// x0*2x1 in full, x1^2 low word; 6 when x1^2 needs its high word) plus per
+// reduction step 4 (u = T0 m', high word of u m0, u m1 in full) twice; per quotient
+// digit 4; plus 8 for m^-1 mod 2^32.  32-bit moduli: 4 per squaring (x^2 in full,
+// u, high word of u m), 2 per digit, 8 for the inverse.
+double head_term_imad(int path, int nb, int first, int lmax);
 
 // Shard `shard` of `nshards` of series j: the head [0, head_end) is cut evenly,
 // the tail [head_end, natural_end) belongs to the last shard.

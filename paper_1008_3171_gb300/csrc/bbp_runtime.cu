@@ -218,11 +218,11 @@ bbp_status launch_ranges(bbp_plan p, int f, uint64_t n, uint32_t W, const std::v
     const uint64_t tile = 32ull * streams * a.run;
     const uint64_t ntiles = (r.count + tile - 1) / tile;
     const int warps_per_block = kHeadThreads / 32;
-    const int occ = head_occupancy(r.wide, streams, lmax);
+    const int occ = head_occupancy(r.path, streams, lmax);
     const uint64_t want = (ntiles + warps_per_block - 1) / warps_per_block;
     const int blocks = static_cast<int>(std::max<uint64_t>(1, std::min<uint64_t>(want, uint64_t(occ) * p->sm_count)));
     if (p->profile) BBP_CUDA(cudaEventRecord(p->ev0, st));
-    BBP_CUDA(launch_head(a, r.wide, streams, lmax, blocks, st));
+    BBP_CUDA(launch_head(a, r.path, streams, lmax, blocks, st));
     if (p->profile) {
       BBP_CUDA(cudaEventRecord(p->ev1, st));
       BBP_CUDA(cudaEventSynchronize(p->ev1));
