@@ -62,7 +62,7 @@ typedef struct bbp_plan_opts {
   uint32_t guard_bits;      /* G: positive multiple of 32; 0 selects 64 */
   size_t accum_mem_budget;  /* bytes of device accumulator memory for queued queries; 0: 64 MiB */
   uint32_t max_slots;       /* concurrent queries admitted by bbp_submit; 0: 4096 */
-  const char* tune_table;   /* path of an autotune table (JSON) or NULL for built-in defaults */
+  const char* tune_table;   /* path of an autotune table (JSON: run, streams, grab) or NULL for defaults */
   uint32_t profile;         /* 1: time head-kernel launches with CUDA events (see bbp_stats) */
   uint32_t strict;          /* 1: bbp_bits fails with BBP_EINVALID_BITS unless all P bits certify */
 } bbp_plan_opts;
@@ -154,6 +154,22 @@ bbp_status bbp_accumulate_async(bbp_plan p, bbp_formula f, uint64_t n, uint32_t 
 bbp_status bbp_finalize_async(bbp_plan p, bbp_formula f, uint64_t n, uint32_t P,
                               const unsigned long long* d_slots, uint8_t* d_out, uint32_t* d_valid,
                               uint32_t* d_limbs, void* stream);
+
+/* A batch of independent queries in one persistent pass.  The paper splits one
+ * huge sum into jobs, tasks and threads (Sec. 4); here many queries of very
+ * different sizes are split into jobs (one range of head terms of one series, or
+ * one tail) that persistent warps consume a few warp tiles at a time from an
+ * atomic queue, small queries first; each query's partial sums stay in its own
+ * device accumulators and the warp that retires its last job finalizes it.  The
+ * pass is captured in a CUDA graph and replayed.  Results are bit-identical to
+ * bbp_bits_formula for each query.
+ * n[count], P[count]: the queries (host arrays).  out: count * out_stride host
+ * bytes, out_stride >= ceil(max P / 8); query q's bits at out + q * out_stride,
+ * MSB first.  valid_bits[count] (may be NULL): certified bits.  latency_ms[count]
+ * (may be NULL): device time from the start of the pass to each query's finalize.
+ * Blocks until done.  EINVAL: a bad query or a too-small out_stride. */
+bbp_status bbp_bits_batch(bbp_plan p, bbp_formula f, uint32_t count, const uint64_t* n, const uint32_t* P,
+                          uint8_t* out, uint32_t out_stride, uint32_t* valid_bits, double* latency_ms);
 
 /* Counters of the last compute call on this plan. */
 bbp_status bbp_plan_stats(bbp_plan p, bbp_stats* out);

@@ -101,6 +101,8 @@ def _load():
         "bbp_finalize_async": ([vp, ctypes.c_int, u64, u32, vp, vp, vp, vp, vp], ctypes.c_int),
         "bbp_imad_probe": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "bbp_partial_sum_noalloc": ([ctypes.c_int, u32, u64, u64, u64, u32, u32, vp, vp], ctypes.c_int),
+        "bbp_bits_batch": ([vp, ctypes.c_int, u32, u64p, u32p, ctypes.c_char_p, u32, u32p,
+                            ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -218,6 +220,33 @@ def bbp_finalize_async(plan: int, formula: int, n: int, P: int, d_slots: int, d_
                        d_limbs: int = 0, stream: Optional[int] = None) -> None:
     _check(_lib.bbp_finalize_async(plan, formula, n, P, d_slots, d_out, d_valid or None, d_limbs or None,
                                    stream or None), "bbp_finalize_async")
+
+
+def bbp_bits_batch(plan: int, formula: int, ns, Ps, with_latency: bool = True):
+    """Batched queries in one persistent pass.  Returns (values, valid, latency_ms):
+    values[q] is the P[q] bits of query q as an integer (MSB = bit n[q])."""
+    count = len(ns)
+    if len(Ps) != count:
+        raise ValueError("ns and Ps differ in length")
+    stride = max(((int(P) + 7) // 8 for P in Ps), default=1)
+    n_arr = (ctypes.c_uint64 * max(count, 1))(*[int(v) for v in ns])
+    p_arr = (ctypes.c_uint32 * max(count, 1))(*[int(v) for v in Ps])
+    out = ctypes.create_string_buffer(max(count, 1) * stride)
+    valid = (ctypes.c_uint32 * max(count, 1))()
+    lat = (ctypes.c_double * max(count, 1))()
+    st = _lib.bbp_bits_batch(plan, formula, count, n_arr, p_arr, out, stride, valid, lat if with_latency else None)
+    if st != BBP_EINVALID_BITS:
+        _check(st, "bbp_bits_batch")
+    raw = out.raw
+    values = []
+    for q in range(count):
+        P = int(Ps[q])
+        nb = (P + 7) // 8
+        values.append(int.from_bytes(raw[q * stride:q * stride + nb], "big") >> (8 * nb - P))
+    result = (values, list(valid)[:count], list(lat)[:count] if with_latency else None)
+    if st == BBP_EINVALID_BITS:
+        raise BBPError(st, "bbp_bits_batch")
+    return result
 
 
 def bbp_plan_stats(plan: int) -> dict:

@@ -71,114 +71,119 @@ __device__ __forceinline__ void fold_digits(uint32_t (&acc)[LMAX], uint32_t (&x0
   }
 }
 
+// One warp tile: terms [ti * tile, (ti + 1) * tile) of the run list of A, added
+// into this lane's sum.  Every lane of the warp must call it (warp-wide reductions).
 template <int LMAX, int PATH, int S>
-__global__ void __launch_bounds__(kHeadThreads) head_kernel(const HeadArgs A, const uint64_t ntiles) {
+__device__ __forceinline__ void process_tile(const HeadArgs& A, const uint64_t ti, const uint32_t lane,
+                                             uint32_t (&acc)[LMAX]) {
   constexpr int NT = 2 * S;
   constexpr bool WIDE = PATH > 0;         // 64-bit moduli (PATH 1: bitlen(m) <= 47, PATH 2: <= 60)
   constexpr bool SMALL = PATH == 1;
   constexpr int RB = WIDE ? 64 : 32;
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t wid = threadIdx.x >> 5;
-  const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
   const uint64_t run = A.run;
   const uint64_t tile = 32ull * S * run;
   const uint64_t last = A.count - 1;
   const int window = static_cast<int>(A.window);
-  // exponent of the first term: E(k) = e0 - step k
+  // exponent of the residue at k: E(k) = e0 - step k
   const uint64_t e0 = A.d + static_cast<int64_t>(A.c) + A.W;
+  uint64_t base[S];
+  StreamState st[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    base[s] = ti * tile + (static_cast<uint64_t>(lane) * S + s) * run;
+    st[s].rel = min(base[s], last);
+    const uint64_t k = A.k_begin + st[s].rel;
+    st[s].m = static_cast<uint64_t>(A.a) * k + A.b;
+    st[s].E = e0 - static_cast<uint64_t>(A.step) * k;
+    st[s].tr = r_mod_m_bitserial<RB>(st[s].m);
+  }
+  for (uint32_t i = 0; i < run; i += 2) {
+    uint64_t v[NT];
+    uint32_t x0[NT], x1[NT], m0[NT], m1[NT], mp[NT], vmask[NT];
+    int nbl = 0;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        const int t = 2 * s + p;
+        const uint64_t rel = base[s] + i + p;
+        const bool valid = rel < A.count;
+        if (valid && rel != st[s].rel) {  // the next k of the run: advance by one
+          st[s].rel = rel;
+          st[s].m += A.a;
+          st[s].E -= A.step;
+          r_mod_m_advance<RB>(st[s].tr, st[s].m, A.a);
+        }
+        x0[t] = lo32(st[s].tr.r);
+        x1[t] = hi32(st[s].tr.r);
+        m0[t] = lo32(st[s].m);
+        m1[t] = hi32(st[s].m);
+        mp[t] = neg_inverse32(m0[t]);
+        vmask[t] = valid ? 0xffffffffu : 0u;
+        v[t] = st[s].E - RB;  // E >= W >= RB for head terms
+        nbl = max(nbl, bitlen64(v[t]));
+      }
+    }
+    const int nb = static_cast<int>(__reduce_max_sync(0xffffffffu, static_cast<uint32_t>(nbl)));
+    const int h = nb > 0 ? min(static_cast<int>(A.first), nb - 1) : 0;
+    const int low = nb - h;  // bits left after the first window
+    uint64_t rem[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      // first window: Montgomery form of 2^w0 is (R mod m) << w0, no squaring
+      const uint32_t w0 = h > 0 ? static_cast<uint32_t>(v[t] >> low) : 0u;
+      if (WIDE) {
+        const uint64_t x = make64(x0[t], x1[t]) << w0;
+        x0[t] = lo32(x);
+        x1[t] = hi32(x);
+      } else {
+        x0[t] <<= w0;
+      }
+      rem[t] = low > 0 ? (v[t] & ((1ull << low) - 1ull)) : 0ull;
+    }
+    // remaining bits, top down, in groups of `window` bits aligned from the top:
+    // len - 1 plain squarings, then one squaring with the group's value shifted in
+    const uint32_t zero[NT] = {};
+    int p = low;
+    while (p > 0) {
+      const int len = min(window, p);
+      p -= len;
+      switch (len) {
+        case 4: square_all<WIDE, SMALL, NT>(x0, x1, m0, m1, mp, zero, false);  // fall through
+        case 3: square_all<WIDE, SMALL, NT>(x0, x1, m0, m1, mp, zero, false);  // fall through
+        case 2: square_all<WIDE, SMALL, NT>(x0, x1, m0, m1, mp, zero, false);  // fall through
+        default: break;
+      }
+      uint32_t sh[NT];
+#pragma unroll
+      for (int t = 0; t < NT; ++t) sh[t] = static_cast<uint32_t>(rem[t] >> p) & ((1u << len) - 1u);
+      square_all<WIDE, SMALL, NT>(x0, x1, m0, m1, mp, sh, true);
+    }
+    // s = 2^E mod m, then the W-bit quotient digits folded into the signed sum
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      if (WIDE) {
+        reduce_once64(x0[t], x1[t], Mod64{m0[t], m1[t], mp[t]});
+      } else if (x0[t] >= m0[t]) {
+        x0[t] -= m0[t];
+      }
+    }
+    if (A.alternating) fold_digits<WIDE, true, NT, LMAX>(acc, x0, x1, m0, m1, mp, vmask);
+    else fold_digits<WIDE, false, NT, LMAX>(acc, x0, x1, m0, m1, mp, vmask);
+  }
+}
+
+template <int LMAX, int PATH, int S>
+__global__ void __launch_bounds__(kHeadThreads) head_kernel(const HeadArgs A, const uint64_t ntiles) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t wid = threadIdx.x >> 5;
+  const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
 
   uint32_t acc[LMAX];
 #pragma unroll
   for (int i = 0; i < LMAX; ++i) acc[i] = 0;
-
-  for (uint64_t ti = warp; ti < ntiles; ti += nwarps) {
-    uint64_t base[S];
-    StreamState st[S];
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-      base[s] = ti * tile + (static_cast<uint64_t>(lane) * S + s) * run;
-      st[s].rel = min(base[s], last);
-      const uint64_t k = A.k_begin + st[s].rel;
-      st[s].m = static_cast<uint64_t>(A.a) * k + A.b;
-      st[s].E = e0 - static_cast<uint64_t>(A.step) * k;
-      st[s].tr = r_mod_m_bitserial<RB>(st[s].m);
-    }
-    for (uint32_t i = 0; i < run; i += 2) {
-      uint64_t v[NT];
-      uint32_t x0[NT], x1[NT], m0[NT], m1[NT], mp[NT], vmask[NT];
-      int nbl = 0;
-#pragma unroll
-      for (int s = 0; s < S; ++s) {
-#pragma unroll
-        for (int p = 0; p < 2; ++p) {
-          const int t = 2 * s + p;
-          const uint64_t rel = base[s] + i + p;
-          const bool valid = rel < A.count;
-          if (valid && rel != st[s].rel) {  // the next k of the run: advance by one
-            st[s].rel = rel;
-            st[s].m += A.a;
-            st[s].E -= A.step;
-            r_mod_m_advance<RB>(st[s].tr, st[s].m, A.a);
-          }
-          x0[t] = lo32(st[s].tr.r);
-          x1[t] = hi32(st[s].tr.r);
-          m0[t] = lo32(st[s].m);
-          m1[t] = hi32(st[s].m);
-          mp[t] = neg_inverse32(m0[t]);
-          vmask[t] = valid ? 0xffffffffu : 0u;
-          v[t] = st[s].E - RB;  // E >= W >= RB for head terms
-          nbl = max(nbl, bitlen64(v[t]));
-        }
-      }
-      const int nb = static_cast<int>(__reduce_max_sync(0xffffffffu, static_cast<uint32_t>(nbl)));
-      const int h = nb > 0 ? min(static_cast<int>(A.first), nb - 1) : 0;
-      const int low = nb - h;  // bits left after the first window
-      uint64_t rem[NT];
-#pragma unroll
-      for (int t = 0; t < NT; ++t) {
-        // first window: Montgomery form of 2^w0 is (R mod m) << w0, no squaring
-        const uint32_t w0 = h > 0 ? static_cast<uint32_t>(v[t] >> low) : 0u;
-        if (WIDE) {
-          const uint64_t x = make64(x0[t], x1[t]) << w0;
-          x0[t] = lo32(x);
-          x1[t] = hi32(x);
-        } else {
-          x0[t] <<= w0;
-        }
-        rem[t] = low > 0 ? (v[t] & ((1ull << low) - 1ull)) : 0ull;
-      }
-      // remaining bits, top down, in groups of `window` bits aligned from the top:
-      // len - 1 plain squarings, then one squaring with the group's value shifted in
-      const uint32_t zero[NT] = {};
-      int p = low;
-      while (p > 0) {
-        const int len = min(window, p);
-        p -= len;
-        switch (len) {
-          case 4: square_all<WIDE, SMALL, NT>(x0, x1, m0, m1, mp, zero, false);  // fall through
-          case 3: square_all<WIDE, SMALL, NT>(x0, x1, m0, m1, mp, zero, false);  // fall through
-          case 2: square_all<WIDE, SMALL, NT>(x0, x1, m0, m1, mp, zero, false);  // fall through
-          default: break;
-        }
-        uint32_t sh[NT];
-#pragma unroll
-        for (int t = 0; t < NT; ++t) sh[t] = static_cast<uint32_t>(rem[t] >> p) & ((1u << len) - 1u);
-        square_all<WIDE, SMALL, NT>(x0, x1, m0, m1, mp, sh, true);
-      }
-      // s = 2^E mod m, then the W-bit quotient digits folded into the signed sum
-#pragma unroll
-      for (int t = 0; t < NT; ++t) {
-        if (WIDE) {
-          reduce_once64(x0[t], x1[t], Mod64{m0[t], m1[t], mp[t]});
-        } else if (x0[t] >= m0[t]) {
-          x0[t] -= m0[t];
-        }
-      }
-      if (A.alternating) fold_digits<WIDE, true, NT, LMAX>(acc, x0, x1, m0, m1, mp, vmask);
-      else fold_digits<WIDE, false, NT, LMAX>(acc, x0, x1, m0, m1, mp, vmask);
-    }
-  }
+  for (uint64_t ti = warp; ti < ntiles; ti += nwarps) process_tile<LMAX, PATH, S>(A, ti, lane, acc);
 
   // limbs at or above L hold digits past 2^W: drop them (the sum is mod 2^W)
 #pragma unroll
@@ -220,16 +225,13 @@ __global__ void __launch_bounds__(kHeadThreads) head_kernel(const HeadArgs A, co
 // floor(2^(W+e)/m) = floor(floor(2^W/m) / 2^-e): the fraction of 1/m, shifted
 // (Sec. 4.3: shift by b bits, then divide to W - b bits).  There are only about
 // W/step of them per series, so one thread per term with plain loops.
-__global__ void tail_kernel(const TailArgs A) {
-  const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (tid >= A.count) return;
-  const uint64_t k = A.k_begin + tid;
+// t (W/32 limbs, signed by (-1)^k and the series sign, mod 2^W) of tail term k.
+__device__ void tail_term(const TailArgs& A, const uint64_t k, uint32_t* t) {
   const int64_t e = static_cast<int64_t>(A.d) + A.c - static_cast<int64_t>(A.step) * static_cast<int64_t>(k);
   const uint32_t L = A.L;
   const int64_t bshift = -e;  // 1 <= bshift <= W
   const uint64_t m = static_cast<uint64_t>(A.a) * k + A.b;
   uint32_t q[kMaxLimbs];
-  uint32_t t[kMaxLimbs];
   for (uint32_t i = 0; i < L; ++i) { q[i] = 0; t[i] = 0; }
   if (e >= 0 || bshift > static_cast<int64_t>(A.W)) return;
   const uint32_t b = static_cast<uint32_t>(bshift);
@@ -255,16 +257,23 @@ __global__ void tail_kernel(const TailArgs A) {
     }
   }
   const bool neg = ((A.alternating && (k & 1ull)) ? 1u : 0u) ^ A.negate;
-  uint64_t carry = 1;
-  for (uint32_t i = 0; i < L; ++i) {
-    uint32_t v = t[i];
-    if (neg) {
-      const uint64_t s = static_cast<uint64_t>(~v) + carry;
-      v = static_cast<uint32_t>(s);
+  if (neg) {
+    uint64_t carry = 1;
+    for (uint32_t i = 0; i < L; ++i) {
+      const uint64_t s = static_cast<uint64_t>(~t[i]) + carry;
+      t[i] = static_cast<uint32_t>(s);
       carry = s >> 32;
     }
-    if (v) atomicAdd(A.slots + i, static_cast<unsigned long long>(v));
   }
+}
+
+__global__ void tail_kernel(const TailArgs A) {
+  const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (tid >= A.count) return;
+  uint32_t t[kMaxLimbs];
+  tail_term(A, A.k_begin + tid, t);
+  for (uint32_t i = 0; i < A.L; ++i)
+    if (t[i]) atomicAdd(A.slots + i, static_cast<unsigned long long>(t[i]));
 }
 
 // ---------------------------------------------------------------- fold / finalize
@@ -320,11 +329,16 @@ __device__ uint32_t certified_bits(const uint32_t* S, int L, uint32_t P, uint64_
   return 0;
 }
 
-__global__ void finalize_bits_kernel(const unsigned long long* slots, int L, uint32_t P, uint64_t bound,
-                                     uint8_t* out, uint32_t* valid, uint32_t* out_limbs) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// S = carry-propagated slots; output bytes (MSB first), certified count, raw limbs.
+__device__ void finalize_into(const unsigned long long* slots, int L, uint32_t P, uint64_t bound, uint8_t* out,
+                              uint32_t* valid, uint32_t* out_limbs) {
   uint32_t S[kMaxLimbs + 1];
-  fold(slots, L, S);
+  unsigned long long carry = 0;
+  for (int i = 0; i < L; ++i) {
+    const unsigned long long v = __ldcg(slots + i) + carry;  // slots were written by atomics
+    S[i] = static_cast<uint32_t>(v);
+    carry = v >> 32;
+  }
   S[L] = 0;
   if (out_limbs)
     for (int i = 0; i < L; ++i) out_limbs[i] = S[i];
@@ -341,6 +355,134 @@ __global__ void finalize_bits_kernel(const unsigned long long* slots, int L, uin
     out[i] = static_cast<uint8_t>(byte);
   }
   if (valid) *valid = certified_bits(S, L, P, bound);
+}
+
+__global__ void finalize_bits_kernel(const unsigned long long* slots, int L, uint32_t P, uint64_t bound,
+                                     uint8_t* out, uint32_t* valid, uint32_t* out_limbs) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  finalize_into(slots, L, P, bound, out, valid, out_limbs);
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// ---------------------------------------------------------------- persistent queue
+
+// Hands out `grab` tiles of the current job to one warp (lane 0 decides, all lanes
+// learn).  Every hand-out either succeeds or moves the cursor past an exhausted
+// job, so the loop ends after at most (jobs left) rounds; nothing waits on other
+// threads.
+__device__ __forceinline__ bool next_grab(const BatchDev& B, uint32_t job_begin, uint32_t job_end,
+                                          unsigned int* cursor, uint32_t lane, uint32_t* job,
+                                          unsigned long long* t0) {
+  uint32_t j = job_end;
+  unsigned long long t = 0;
+  if (lane == 0) {
+    for (;;) {
+      const uint32_t rel = *reinterpret_cast<volatile unsigned int*>(cursor);
+      j = job_begin + rel;
+      if (j >= job_end) { j = job_end; break; }
+      t = atomicAdd(B.job_taken + j, static_cast<unsigned long long>(B.grab));
+      if (t < B.job_tiles[j]) break;
+      atomicMax(cursor, rel + 1);
+    }
+  }
+  j = __shfl_sync(0xffffffffu, j, 0);
+  t = __shfl_sync(0xffffffffu, t, 0);
+  *job = j;
+  *t0 = t;
+  return j < job_end;
+}
+
+// Called by one thread after its part of query q's last job is in the
+// accumulators (and fenced): the thread that retires the query's last job
+// finalizes it.
+__device__ void retire_job(const BatchDev& B, uint32_t q) {
+  if (atomicSub(B.jobs_left + q, 1u) == 1u) {
+    __threadfence();
+    const QueryDesc Q = B.queries[q];
+    finalize_into(B.accum + static_cast<uint64_t>(q) * kMaxLimbs, static_cast<int>(Q.L), Q.P, Q.bound,
+                  B.out + Q.out_offset, B.valid + q, nullptr);
+    B.done_ns[q] = global_ns();
+  }
+}
+
+template <int LMAX, int PATH, int S>
+__global__ void __launch_bounds__(kHeadThreads) queue_kernel(const BatchDev B, const uint32_t job_begin,
+                                                             const uint32_t job_end, unsigned int* cursor) {
+  const uint32_t lane = threadIdx.x & 31u;
+  // the warp's current job lives in shared memory (like kernel arguments, it is
+  // read-only and uniform, so it need not occupy registers)
+  __shared__ HeadArgs job_sm[kHeadThreads / 32];
+  HeadArgs& A = job_sm[threadIdx.x >> 5];
+  uint32_t j;
+  unsigned long long t0;
+  while (next_grab(B, job_begin, job_end, cursor, lane, &j, &t0)) {
+    static_assert(sizeof(HeadArgs) % 4 == 0, "HeadArgs is copied as 32-bit words");
+    {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(B.jobs + j);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(&A);
+      for (uint32_t w = lane; w < sizeof(HeadArgs) / 4; w += 32) dst[w] = src[w];
+      __syncwarp();
+    }
+    const unsigned long long ntiles = B.job_tiles[j];
+    const unsigned long long t1 = min(t0 + B.grab, ntiles);
+    uint32_t acc[LMAX];
+#pragma unroll
+    for (int i = 0; i < LMAX; ++i) acc[i] = 0;
+    for (unsigned long long ti = t0; ti < t1; ++ti) process_tile<LMAX, PATH, S>(A, ti, lane, acc);
+#pragma unroll
+    for (int i = 0; i < LMAX; ++i)
+      if (i >= static_cast<int>(A.L)) acc[i] = 0;
+    warp_sum_limbs<LMAX>(acc);
+    if (lane == 0) {
+      if (A.negate) {
+        uint64_t carry = 1;
+#pragma unroll
+        for (int i = 0; i < LMAX; ++i) {
+          const uint64_t v = static_cast<uint64_t>(~acc[i]) + carry;
+          acc[i] = static_cast<uint32_t>(v);
+          carry = v >> 32;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < LMAX; ++i)
+        if (i < static_cast<int>(A.L) && acc[i]) atomicAdd(A.slots + i, static_cast<unsigned long long>(acc[i]));
+      __threadfence();
+      const unsigned long long done = atomicAdd(B.job_done + j, t1 - t0) + (t1 - t0);
+      if (done == ntiles) retire_job(B, B.job_query[j]);
+    }
+    __syncwarp();
+  }
+}
+
+__global__ void timestamp_kernel(unsigned long long* where) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *where = global_ns();
+}
+
+// Tail jobs: one warp per job, one term per lane at a time.
+__global__ void queue_tail_kernel(const BatchDev B) {
+  const uint32_t lane = threadIdx.x & 31u;
+  for (;;) {
+    uint32_t j = 0;
+    if (lane == 0) j = atomicAdd(B.tail_cursor, 1u);
+    j = __shfl_sync(0xffffffffu, j, 0);
+    if (j >= B.ntails) break;
+    const TailArgs A = B.tails[j];
+    uint32_t t[kMaxLimbs];
+    for (uint64_t i = lane; i < A.count; i += 32) {
+      tail_term(A, A.k_begin + i, t);
+      for (uint32_t l = 0; l < A.L; ++l)
+        if (t[l]) atomicAdd(A.slots + l, static_cast<unsigned long long>(t[l]));
+    }
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) retire_job(B, B.tail_query[j]);
+    __syncwarp();
+  }
 }
 
 // ---------------------------------------------------------------- IMAD probe
@@ -446,6 +588,80 @@ int head_occupancy(int path, int streams, int lmax) {
     case 40: return occupancy_l<40>(path, streams);
     default: return 1;
   }
+}
+
+namespace {
+template <int LMAX, int PATH, int S>
+int queue_occupancy_t() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, queue_kernel<LMAX, PATH, S>, kHeadThreads, 0) != cudaSuccess)
+    return 1;
+  return n > 0 ? n : 1;
+}
+
+template <int LMAX, int PATH>
+int queue_occupancy_p(int streams) {
+  return streams == 2 ? queue_occupancy_t<LMAX, PATH, 2>() : queue_occupancy_t<LMAX, PATH, 1>();
+}
+
+template <int LMAX>
+int queue_occupancy_l(int path, int streams) {
+  if (path == 2) return queue_occupancy_p<LMAX, 2>(streams);
+  if (path == 1) return queue_occupancy_p<LMAX, 1>(streams);
+  return queue_occupancy_p<LMAX, 0>(streams);
+}
+
+template <int LMAX, int PATH>
+cudaError_t launch_queue_p(const BatchDev& b, uint32_t jb, uint32_t je, unsigned int* cursor, int streams,
+                           int blocks, cudaStream_t s) {
+  if (streams == 2) queue_kernel<LMAX, PATH, 2><<<blocks, kHeadThreads, 0, s>>>(b, jb, je, cursor);
+  else queue_kernel<LMAX, PATH, 1><<<blocks, kHeadThreads, 0, s>>>(b, jb, je, cursor);
+  return cudaGetLastError();
+}
+
+template <int LMAX>
+cudaError_t launch_queue_l(const BatchDev& b, uint32_t jb, uint32_t je, unsigned int* cursor, int path, int streams,
+                           int blocks, cudaStream_t s) {
+  if (path == 2) return launch_queue_p<LMAX, 2>(b, jb, je, cursor, streams, blocks, s);
+  if (path == 1) return launch_queue_p<LMAX, 1>(b, jb, je, cursor, streams, blocks, s);
+  return launch_queue_p<LMAX, 0>(b, jb, je, cursor, streams, blocks, s);
+}
+}  // namespace
+
+int queue_occupancy(int path, int streams, int lmax) {
+  switch (lmax) {
+    case 3: return queue_occupancy_l<3>(path, streams);
+    case 4: return queue_occupancy_l<4>(path, streams);
+    case 6: return queue_occupancy_l<6>(path, streams);
+    case 10: return queue_occupancy_l<10>(path, streams);
+    case 16: return queue_occupancy_l<16>(path, streams);
+    case 40: return queue_occupancy_l<40>(path, streams);
+    default: return 1;
+  }
+}
+
+cudaError_t launch_queue(const BatchDev& b, uint32_t job_begin, uint32_t job_end, unsigned int* cursor, int path,
+                         int streams, int lmax, int blocks, cudaStream_t s) {
+  switch (lmax) {
+    case 3: return launch_queue_l<3>(b, job_begin, job_end, cursor, path, streams, blocks, s);
+    case 4: return launch_queue_l<4>(b, job_begin, job_end, cursor, path, streams, blocks, s);
+    case 6: return launch_queue_l<6>(b, job_begin, job_end, cursor, path, streams, blocks, s);
+    case 10: return launch_queue_l<10>(b, job_begin, job_end, cursor, path, streams, blocks, s);
+    case 16: return launch_queue_l<16>(b, job_begin, job_end, cursor, path, streams, blocks, s);
+    case 40: return launch_queue_l<40>(b, job_begin, job_end, cursor, path, streams, blocks, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_timestamp(unsigned long long* where, cudaStream_t s) {
+  timestamp_kernel<<<1, 32, 0, s>>>(where);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_queue_tail(const BatchDev& b, int blocks, cudaStream_t s) {
+  if (b.ntails == 0) return cudaSuccess;
+  queue_tail_kernel<<<blocks, 128, 0, s>>>(b);
+  return cudaGetLastError();
 }
 
 int head_lmax_for(int L) {

@@ -43,6 +43,40 @@ struct TailArgs {
 constexpr int kMaxLimbs = 40;    // W <= 1280 bits
 constexpr int kHeadThreads = 256;
 
+// ---------------------------------------------------------------- batches
+//
+// A batch of queries is a list of jobs: head jobs (one HeadArgs each: a range of
+// head terms of one series of one query, whose `slots` point at that query's
+// accumulators) grouped by kernel variant, plus tail jobs.  Persistent warps hand
+// out `grab` tiles of the current job at a time; the warp that finishes a query's
+// last job finalizes the query.
+struct QueryDesc {
+  uint64_t bound;       // N + J + 1: |S - exact| < bound units
+  uint32_t P;           // output bits
+  uint32_t L;           // limbs of the working precision
+  uint32_t out_offset;  // byte offset of the query's output bits in `out`
+  uint32_t pad;
+};
+
+struct BatchDev {
+  const HeadArgs* jobs;            // head jobs, grouped by kernel variant
+  const uint32_t* job_query;       // query index of each head job
+  const uint64_t* job_tiles;       // warp tiles of each head job
+  unsigned long long* job_taken;   // tiles handed out so far (atomic)
+  unsigned long long* job_done;    // tiles finished so far (atomic)
+  const TailArgs* tails;           // tail jobs
+  const uint32_t* tail_query;
+  uint32_t ntails;
+  uint32_t grab;                   // tiles per hand-out
+  unsigned int* tail_cursor;       // next tail job (atomic)
+  const QueryDesc* queries;
+  unsigned long long* accum;       // kMaxLimbs carry-save accumulators per query
+  unsigned int* jobs_left;         // unfinished jobs (head + tail) per query (atomic)
+  uint8_t* out;                    // output bits of every query
+  uint32_t* valid;                 // certified bit count per query
+  unsigned long long* done_ns;     // completion time per query (device global timer, ns)
+};
+
 // Launch helpers (defined in bbp_kernels.cu).  They return cudaGetLastError().
 // path: 0 = 32-bit moduli (bitlen <= 29), 1 = 64-bit moduli with bitlen <= 47,
 //       2 = 64-bit moduli with bitlen <= 60.
@@ -52,6 +86,13 @@ cudaError_t launch_zero_slots(unsigned long long* slots, int L, cudaStream_t s);
 cudaError_t launch_fold_limbs(const unsigned long long* slots, int L, uint32_t* out_limbs, cudaStream_t s);
 cudaError_t launch_finalize_bits(const unsigned long long* slots, int L, uint32_t P, uint64_t bound,
                                  uint8_t* out_bytes, uint32_t* valid_bits, uint32_t* out_limbs, cudaStream_t s);
+// One persistent launch over the head jobs [job_begin, job_end) of one variant;
+// *cursor (relative to job_begin) must be 0.  blocks = resident CTAs.
+cudaError_t launch_queue(const BatchDev& b, uint32_t job_begin, uint32_t job_end, unsigned int* cursor, int path,
+                         int streams, int lmax, int blocks, cudaStream_t s);
+cudaError_t launch_queue_tail(const BatchDev& b, int blocks, cudaStream_t s);
+cudaError_t launch_timestamp(unsigned long long* where, cudaStream_t s);
+int queue_occupancy(int path, int streams, int lmax);
 int head_lmax_for(int L);  // smallest compiled limb capacity >= L, or 0
 int head_occupancy(int path, int streams, int lmax);  // resident CTAs per SM of that instantiation
 cudaError_t launch_imad_probe(int kind, int blocks, int threads, int iters, unsigned long long* cycles_out,

@@ -409,7 +409,3 @@ bbp_status bbp_imad_probe(bbp_plan p, int kind, double* lanes_per_clk_per_sm) {
 }
 
 }  // extern "C"
-
-namespace bbp {
-void release_batch_state(bbp_plan) {}
-}  // namespace bbp

@@ -22,6 +22,7 @@ struct bbp_plan_s {
   // head-kernel tuning (terms per stream run, streams per thread)
   int run = 32;
   int streams = 1;
+  int grab = 8;  // batched pass: warp tiles handed out per queue operation
   // single-query buffers
   unsigned long long* d_slots = nullptr;  // kMaxLimbs carry-save accumulators
   uint32_t* d_limbs = nullptr;
