@@ -47,6 +47,10 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--workload", choices=["single", "batched"], default="single",
+                    help="single: the n=1e12 headline; batched: 4096 seeded queries, persistent vs plain")
+    ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--tune-table", default=None)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target wall time of one oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -344,10 +348,74 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- batched workload
+
+def percentile(values, q):
+    v = sorted(values)
+    if not v:
+        return None
+    i = min(len(v) - 1, max(0, int(round(q / 100.0 * (len(v) - 1)))))
+    return v[i]
+
+
+def run_batched(args):
+    """4096 seeded queries (n log-uniform in [1e4, 1e10], P in {64, 128, 256}, G = 64):
+    one persistent graph-captured pass (bbp_bits_batch) against the plain form (one
+    bbp_bits call per query, in submission order); outputs must be identical."""
+    import torch
+
+    import paper_1008_3171_gb300 as bbp
+    import workloads
+
+    ns, Ps = workloads.batched_queries(count=args.batch_count, seed=0)
+    plan = bbp.Plan(device=0, guard_bits=GUARD, tune_table=args.tune_table)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        bbp.bbp_bits_batch(plan.handle, 0, ns, Ps, with_latency=False)
+    sampler = ClockSampler(0)
+    sampler.start()
+    per = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        vals, valid, lat = bbp.bbp_bits_batch(plan.handle, 0, ns, Ps)
+        per.append(time.perf_counter() - t0)
+    batch_stats = plan.stats()
+    terms = batch_stats["terms"]
+    flush.fill_(2)
+    torch.cuda.synchronize()
+    plain_lat = []
+    plain_vals = []
+    t0 = time.perf_counter()
+    for n, P in zip(ns, Ps):
+        v, ok = plan.bits(n, P)
+        plain_vals.append((v, ok))
+        plain_lat.append(1e3 * (time.perf_counter() - t0))
+    plain_s = time.perf_counter() - t0
+    clocks = sampler.stop()
+    identical = plain_vals == list(zip(vals, valid))
+    t = sum(per) / len(per)
+    emit({
+        "metric": "batched: terms/s and p50/p99 query latency, persistent vs plain", "workload": "batched",
+        "config": {"queries": len(ns), "seed": 0, "n": "floor(10^U(4,10))", "P": "uniform {64,128,256}",
+                   "guard_bits": GUARD, "terms": terms, "tune_table": args.tune_table},
+        "persistent": {"terms_per_s": terms / t, "wall_s": t, "p50_ms": percentile(lat, 50),
+                       "p99_ms": percentile(lat, 99), "latency": "device time from pass start to each finalize",
+                       "launches": batch_stats["kernel_launches"], "steps": args.steps, "warmup": args.warmup},
+        "plain": {"terms_per_s": terms / plain_s, "wall_s": plain_s, "p50_ms": percentile(plain_lat, 50),
+                  "p99_ms": percentile(plain_lat, 99), "latency": "host time from start to each bbp_bits return"},
+        "identical": identical, "all_certified": all(ok == P for (v, ok), P in zip(plain_vals, Ps)),
+        "clocks": clocks,
+    })
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_gpu(args)
 

@@ -2,11 +2,12 @@
 //
 // Every query of a batch is planned into jobs (bbp_planner.cpp): head jobs -- one
 // range of head terms of one series, with the ladder parameters of its moduli --
-// and tail jobs.  Head jobs are grouped by kernel variant (limb capacity x modulus
-// path) and ordered small query first; each variant gets one persistent launch in
-// which warps take `grab` tiles of the current job at a time (queue_kernel), so
-// queries of very different sizes share the GPU at tile granularity and small ones
-// finish early.  Each query's signed partial sums accumulate in its own carry-save
+// and tail jobs.  Queries are sorted by size and cut into waves whose work grows
+// geometrically (the smallest queries first); a wave is one tail launch plus one
+// persistent launch per kernel variant (limb capacity x modulus path) in which
+// warps take `grab` tiles of the current job at a time (queue_kernel), so queries
+// of very different sizes share the GPU at tile granularity and small ones finish
+// early.  Each query's signed partial sums accumulate in its own carry-save
 // slots; the warp that retires its last job finalizes it on the device and stamps
 // the completion time.  The whole pass -- uploads, resets, launches, downloads --
 // is captured once into a CUDA graph and replayed (the executable graph is updated
@@ -83,7 +84,7 @@ struct BatchState {
   uint8_t* d_out = nullptr;                 size_t c_out = 0;
   uint32_t* d_valid = nullptr;              size_t c_valid = 0;
   unsigned long long* d_done = nullptr;     size_t c_done = 0;   // [0] = start time, [1 + q] = done
-  unsigned int* d_cursors = nullptr;        // kVariants + 1 (tail)
+  unsigned int* d_cursors = nullptr;        size_t c_cursors = 0;  // per wave: kVariants + 1 (tail)
   // pinned host staging
   HeadArgs* h_jobs = nullptr;               size_t hc_jobs = 0;
   uint32_t* h_job_query = nullptr;          size_t hc_job_query = 0;
@@ -135,10 +136,13 @@ void release_batch_state(bbp_plan p) {
   p->batch = nullptr;
 }
 
+constexpr int kMaxWaves = 16;
+
 // Plans `count` queries into the batch's pinned staging buffers.
 struct BatchPlan {
-  uint32_t njobs = 0, ntails = 0;
-  uint32_t variant_begin[kVariants + 1] = {};
+  uint32_t njobs = 0, ntails = 0, nwaves = 0;
+  uint32_t group_begin[kMaxWaves * kVariants + 1] = {};  // head jobs of (wave, variant)
+  uint32_t tail_begin[kMaxWaves + 1] = {};               // tail jobs of a wave
   uint64_t terms = 0, head_terms = 0;
   double imad = 0;
 };
@@ -232,7 +236,28 @@ static bbp_status plan_batch(bbp_plan p, int f, uint32_t count, const uint64_t* 
     Q.L = L;
     Q.out_offset = q * kOutStride;
   }
-  // small queries first inside each variant (latency), stable in k
+  // waves: queries by size, each wave at least twice the work of the ones before it
+  std::vector<uint32_t> qorder(count);
+  std::iota(qorder.begin(), qorder.end(), 0u);
+  std::stable_sort(qorder.begin(), qorder.end(), [&](uint32_t x, uint32_t y) { return qterms[x] < qterms[y]; });
+  std::vector<uint32_t> wave_of(count, 0);
+  {
+    uint64_t total = 0;
+    for (uint64_t t : qterms) total += t;
+    const uint64_t first = std::max<uint64_t>(total / 4096, 1);  // the first wave: 1/4096 of the work
+    uint64_t done = 0, target = first;
+    uint32_t w = 0;
+    for (uint32_t i = 0; i < count; ++i) {
+      const uint32_t q = qorder[i];
+      if (done >= target && w + 1 < static_cast<uint32_t>(kMaxWaves)) {
+        ++w;
+        target = std::max(target, done) * 2;
+      }
+      wave_of[q] = w;
+      done += qterms[q];
+    }
+    bp->nwaves = w + 1;
+  }
   uint32_t nj = 0;
   for (int v = 0; v < kVariants; ++v) nj += static_cast<uint32_t>(vj[v].size());
   if (!grow_host(&b->h_jobs, &b->hc_jobs, nj) || !grow_host(&b->h_job_query, &b->hc_job_query, nj) ||
@@ -241,24 +266,36 @@ static bbp_status plan_batch(bbp_plan p, int f, uint32_t count, const uint64_t* 
       !grow_host(&b->h_queries, &b->hc_queries, count) || !grow_host(&b->h_jobs_left, &b->hc_jobs_left, count))
     return BBP_ENOMEM;
   uint32_t at = 0;
-  for (int v = 0; v < kVariants; ++v) {
-    bp->variant_begin[v] = at;
-    std::vector<uint32_t> order(vj[v].size());
-    std::iota(order.begin(), order.end(), 0u);
-    std::stable_sort(order.begin(), order.end(),
-                     [&](uint32_t x, uint32_t y) { return qterms[vq[v][x]] < qterms[vq[v][y]]; });
-    for (uint32_t i : order) {
-      b->h_jobs[at] = vj[v][i];
-      b->h_job_query[at] = vq[v][i];
-      b->h_job_tiles[at] = vt[v][i];
-      ++at;
+  for (uint32_t w = 0; w < bp->nwaves; ++w) {
+    for (int v = 0; v < kVariants; ++v) {
+      bp->group_begin[w * kVariants + v] = at;
+      std::vector<uint32_t> order;
+      for (uint32_t i = 0; i < vj[v].size(); ++i)
+        if (wave_of[vq[v][i]] == w) order.push_back(i);
+      std::stable_sort(order.begin(), order.end(),
+                       [&](uint32_t x, uint32_t y) { return qterms[vq[v][x]] < qterms[vq[v][y]]; });
+      for (uint32_t i : order) {
+        b->h_jobs[at] = vj[v][i];
+        b->h_job_query[at] = vq[v][i];
+        b->h_job_tiles[at] = vt[v][i];
+        ++at;
+      }
     }
   }
-  bp->variant_begin[kVariants] = at;
+  bp->group_begin[bp->nwaves * kVariants] = at;
+  uint32_t tat = 0;
+  for (uint32_t w = 0; w < bp->nwaves; ++w) {
+    bp->tail_begin[w] = tat;
+    for (size_t i = 0; i < tails.size(); ++i)
+      if (wave_of[tail_q[i]] == w) {
+        b->h_tails[tat] = tails[i];
+        b->h_tail_query[tat] = tail_q[i];
+        ++tat;
+      }
+  }
+  bp->tail_begin[bp->nwaves] = tat;
   bp->njobs = nj;
   bp->ntails = static_cast<uint32_t>(tails.size());
-  std::copy(tails.begin(), tails.end(), b->h_tails);
-  std::copy(tail_q.begin(), tail_q.end(), b->h_tail_query);
   std::copy(queries.begin(), queries.end(), b->h_queries);
   std::copy(jobs_left.begin(), jobs_left.end(), b->h_jobs_left);
   return BBP_OK;
@@ -293,7 +330,7 @@ extern "C" bbp_status bbp_bits_batch(bbp_plan p, bbp_formula f, uint32_t count, 
       !grow_host(&b->h_out, &b->hc_out, static_cast<size_t>(count) * kOutStride) ||
       !grow_host(&b->h_valid, &b->hc_valid, count) || !grow_host(&b->h_done, &b->hc_done, count + 1ull))
     return BBP_ENOMEM;
-  if (!b->d_cursors && cudaMalloc(&b->d_cursors, sizeof(unsigned int) * (kVariants + 1)) != cudaSuccess)
+  if (!grow_device(&b->d_cursors, &b->c_cursors, static_cast<size_t>(kMaxWaves) * (kVariants + 1)))
     return BBP_ENOMEM;
   (void)old_accum;
   BatchPlan bp;
@@ -313,9 +350,7 @@ extern "C" bbp_status bbp_bits_batch(bbp_plan p, bbp_formula f, uint32_t count, 
   dev.job_done = b->d_job_ctr + bp.njobs;
   dev.tails = b->d_tails;
   dev.tail_query = b->d_tail_query;
-  dev.ntails = bp.ntails;
   dev.grab = static_cast<uint32_t>(p->grab);
-  dev.tail_cursor = b->d_cursors + kVariants;
   dev.queries = b->d_queries;
   dev.accum = b->d_accum;
   dev.jobs_left = b->d_jobs_left;
@@ -342,20 +377,26 @@ extern "C" bbp_status bbp_bits_batch(bbp_plan p, bbp_formula f, uint32_t count, 
   chk(cudaMemcpyAsync(b->d_queries, b->h_queries, sizeof(QueryDesc) * count, cudaMemcpyHostToDevice, s));
   chk(cudaMemcpyAsync(b->d_jobs_left, b->h_jobs_left, sizeof(unsigned int) * count, cudaMemcpyHostToDevice, s));
   chk(cudaMemsetAsync(b->d_job_ctr, 0, sizeof(unsigned long long) * 2 * bp.njobs, s));
-  chk(cudaMemsetAsync(b->d_cursors, 0, sizeof(unsigned int) * (kVariants + 1), s));
+  chk(cudaMemsetAsync(b->d_cursors, 0, sizeof(unsigned int) * kMaxWaves * (kVariants + 1), s));
   chk(cudaMemsetAsync(b->d_accum, 0, sizeof(unsigned long long) * kMaxLimbs * count, s));
   chk(launch_timestamp(b->d_done, s));
-  uint64_t launches = 1;
-  for (int v = 0; v < kVariants; ++v) {
-    const uint32_t jb = bp.variant_begin[v], je = bp.variant_begin[v + 1];
-    if (jb == je) continue;
-    const int lmax = kLmaxClasses[v / 3], path = v % 3;
-    const int blocks = queue_occupancy(path, p->streams, lmax) * p->sm_count;
-    chk(launch_queue(dev, jb, je, b->d_cursors + v, path, p->streams, lmax, blocks, s));
-    ++launches;
+  uint64_t launches = 1, head_launches = 0;
+  for (uint32_t w = 0; w < bp.nwaves; ++w) {
+    unsigned int* cur = b->d_cursors + static_cast<size_t>(w) * (kVariants + 1);
+    if (bp.tail_begin[w] < bp.tail_begin[w + 1]) {
+      chk(launch_queue_tail(dev, bp.tail_begin[w], bp.tail_begin[w + 1], cur + kVariants, p->sm_count * 4, s));
+      ++launches;
+    }
+    for (int v = 0; v < kVariants; ++v) {
+      const uint32_t jb = bp.group_begin[w * kVariants + v], je = bp.group_begin[w * kVariants + v + 1];
+      if (jb == je) continue;
+      const int lmax = kLmaxClasses[v / 3], path = v % 3;
+      const int blocks = queue_occupancy(path, p->streams, lmax) * p->sm_count;
+      chk(launch_queue(dev, jb, je, cur + v, path, p->streams, lmax, blocks, s));
+      ++launches;
+      ++head_launches;
+    }
   }
-  chk(launch_queue_tail(dev, p->sm_count * 4, s));
-  ++launches;
   chk(cudaMemcpyAsync(b->h_out, b->d_out, static_cast<size_t>(count) * kOutStride, cudaMemcpyDeviceToHost, s));
   chk(cudaMemcpyAsync(b->h_valid, b->d_valid, sizeof(uint32_t) * count, cudaMemcpyDeviceToHost, s));
   chk(cudaMemcpyAsync(b->h_done, b->d_done, sizeof(unsigned long long) * (count + 1ull), cudaMemcpyDeviceToHost, s));
@@ -387,7 +428,7 @@ extern "C" bbp_status bbp_bits_batch(bbp_plan p, bbp_formula f, uint32_t count, 
   p->stats = bbp_stats{};
   p->stats.terms = bp.terms;
   p->stats.head_terms = bp.head_terms;
-  p->stats.head_launches = launches - 2;
+  p->stats.head_launches = head_launches;
   p->stats.kernel_launches = launches;
   p->stats.imad_model = bp.imad;
   if (p->profile) {

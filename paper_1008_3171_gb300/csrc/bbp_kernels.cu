@@ -464,13 +464,14 @@ __global__ void timestamp_kernel(unsigned long long* where) {
 }
 
 // Tail jobs: one warp per job, one term per lane at a time.
-__global__ void queue_tail_kernel(const BatchDev B) {
+__global__ void queue_tail_kernel(const BatchDev B, const uint32_t tail_begin, const uint32_t tail_end,
+                                  unsigned int* cursor) {
   const uint32_t lane = threadIdx.x & 31u;
   for (;;) {
     uint32_t j = 0;
-    if (lane == 0) j = atomicAdd(B.tail_cursor, 1u);
+    if (lane == 0) j = tail_begin + atomicAdd(cursor, 1u);
     j = __shfl_sync(0xffffffffu, j, 0);
-    if (j >= B.ntails) break;
+    if (j >= tail_end) break;
     const TailArgs A = B.tails[j];
     uint32_t t[kMaxLimbs];
     for (uint64_t i = lane; i < A.count; i += 32) {
@@ -658,9 +659,10 @@ cudaError_t launch_timestamp(unsigned long long* where, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_queue_tail(const BatchDev& b, int blocks, cudaStream_t s) {
-  if (b.ntails == 0) return cudaSuccess;
-  queue_tail_kernel<<<blocks, 128, 0, s>>>(b);
+cudaError_t launch_queue_tail(const BatchDev& b, uint32_t tail_begin, uint32_t tail_end, unsigned int* cursor,
+                              int blocks, cudaStream_t s) {
+  if (tail_begin >= tail_end) return cudaSuccess;
+  queue_tail_kernel<<<blocks, 128, 0, s>>>(b, tail_begin, tail_end, cursor);
   return cudaGetLastError();
 }
 

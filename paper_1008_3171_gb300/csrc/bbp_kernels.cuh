@@ -66,9 +66,7 @@ struct BatchDev {
   unsigned long long* job_done;    // tiles finished so far (atomic)
   const TailArgs* tails;           // tail jobs
   const uint32_t* tail_query;
-  uint32_t ntails;
   uint32_t grab;                   // tiles per hand-out
-  unsigned int* tail_cursor;       // next tail job (atomic)
   const QueryDesc* queries;
   unsigned long long* accum;       // kMaxLimbs carry-save accumulators per query
   unsigned int* jobs_left;         // unfinished jobs (head + tail) per query (atomic)
@@ -90,7 +88,9 @@ cudaError_t launch_finalize_bits(const unsigned long long* slots, int L, uint32_
 // *cursor (relative to job_begin) must be 0.  blocks = resident CTAs.
 cudaError_t launch_queue(const BatchDev& b, uint32_t job_begin, uint32_t job_end, unsigned int* cursor, int path,
                          int streams, int lmax, int blocks, cudaStream_t s);
-cudaError_t launch_queue_tail(const BatchDev& b, int blocks, cudaStream_t s);
+// Tail jobs [tail_begin, tail_end); *cursor (relative to tail_begin) must be 0.
+cudaError_t launch_queue_tail(const BatchDev& b, uint32_t tail_begin, uint32_t tail_end, unsigned int* cursor,
+                              int blocks, cudaStream_t s);
 cudaError_t launch_timestamp(unsigned long long* where, cudaStream_t s);
 int queue_occupancy(int path, int streams, int lmax);
 int head_lmax_for(int L);  // smallest compiled limb capacity >= L, or 0
