@@ -171,6 +171,39 @@ bbp_status bbp_finalize_async(bbp_plan p, bbp_formula f, uint64_t n, uint32_t P,
 bbp_status bbp_bits_batch(bbp_plan p, bbp_formula f, uint32_t count, const uint64_t* n, const uint32_t* P,
                           uint8_t* out, uint32_t out_stride, uint32_t* valid_bits, double* latency_ms);
 
+/* ---- serving: continuous batching of bit-position queries ----
+ * An engine thread owned by the plan admits submitted queries into device
+ * accumulator slots (at most min(max_slots, accum_mem_budget / 512 B) at once)
+ * and runs short iterations; each iteration takes from every admitted query a
+ * piece of its remaining terms (a fair share of an iteration budget sized from
+ * the measured throughput), so long queries are sliced and queries that arrive
+ * meanwhile join the next iteration.  Partial sums stay on the device between
+ * iterations; the device finalizes a query in the iteration that runs its last
+ * piece.  Results are bit-identical to bbp_bits.  bbp_submit/bbp_poll/
+ * bbp_serve_stats may be called from any host thread.  (The paper's analogue is
+ * its controller submitting small jobs into free cluster slots, Sec. 4.4.) */
+typedef uint64_t bbp_ticket;
+
+/* Queues the query (bits n .. n+P-1 by Eq. 2).  BBP_EBUSY: the wait queue is as
+ * long as the slot pool; retry later.  EINVAL/ERANGE as bbp_bits. */
+bbp_status bbp_submit(bbp_plan p, uint64_t n, uint32_t P, bbp_ticket* t);
+
+/* BBP_PENDING while the query runs; BBP_OK once done, then out (ceil(P/8) host
+ * bytes, MSB first) and valid_bits (may be NULL) are filled and the ticket is
+ * released; BBP_ENOTFOUND for an unknown or already collected ticket. */
+bbp_status bbp_poll(bbp_plan p, bbp_ticket t, uint8_t* out, uint32_t* valid_bits);
+
+typedef struct bbp_serve_info {
+  uint64_t pending;      /* submitted, waiting for a slot */
+  uint64_t active;       /* in slots, partly evaluated */
+  uint64_t slots;        /* size of the slot pool */
+  uint64_t iterations;   /* iterations run so far */
+  uint64_t terms;        /* terms evaluated so far */
+  double terms_per_s;    /* smoothed throughput of recent iterations */
+} bbp_serve_info;
+
+bbp_status bbp_serve_stats(bbp_plan p, bbp_serve_info* info);
+
 /* Counters of the last compute call on this plan. */
 bbp_status bbp_plan_stats(bbp_plan p, bbp_stats* out);
 

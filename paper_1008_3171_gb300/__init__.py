@@ -55,6 +55,17 @@ class bbp_plan_opts(ctypes.Structure):
     ]
 
 
+class bbp_serve_info(ctypes.Structure):
+    _fields_ = [
+        ("pending", ctypes.c_uint64),
+        ("active", ctypes.c_uint64),
+        ("slots", ctypes.c_uint64),
+        ("iterations", ctypes.c_uint64),
+        ("terms", ctypes.c_uint64),
+        ("terms_per_s", ctypes.c_double),
+    ]
+
+
 class bbp_stats(ctypes.Structure):
     _fields_ = [
         ("terms", ctypes.c_uint64),
@@ -103,6 +114,9 @@ def _load():
         "bbp_partial_sum_noalloc": ([ctypes.c_int, u32, u64, u64, u64, u32, u32, vp, vp], ctypes.c_int),
         "bbp_bits_batch": ([vp, ctypes.c_int, u32, u64p, u32p, ctypes.c_char_p, u32, u32p,
                             ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "bbp_submit": ([vp, u64, u32, u64p], ctypes.c_int),
+        "bbp_poll": ([vp, u64, ctypes.c_char_p, u32p], ctypes.c_int),
+        "bbp_serve_stats": ([vp, ctypes.POINTER(bbp_serve_info)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -247,6 +261,33 @@ def bbp_bits_batch(plan: int, formula: int, ns, Ps, with_latency: bool = True):
     if st == BBP_EINVALID_BITS:
         raise BBPError(st, "bbp_bits_batch")
     return result
+
+
+def bbp_submit(plan: int, n: int, P: int) -> Optional[int]:
+    """Ticket of the queued query, or None when the engine is busy (BBP_EBUSY)."""
+    t = ctypes.c_uint64()
+    st = _lib.bbp_submit(plan, n, P, ctypes.byref(t))
+    if st == BBP_EBUSY:
+        return None
+    _check(st, "bbp_submit")
+    return t.value
+
+
+def bbp_poll(plan: int, ticket: int, P: int) -> Optional[tuple[int, int]]:
+    """None while pending; else (the P bits as an integer, certified bit count)."""
+    out = ctypes.create_string_buffer((P + 7) // 8)
+    valid = ctypes.c_uint32()
+    st = _lib.bbp_poll(plan, ticket, out, ctypes.byref(valid))
+    if st == BBP_PENDING:
+        return None
+    _check(st, "bbp_poll")
+    return int.from_bytes(out.raw, "big") >> (8 * len(out.raw) - P), valid.value
+
+
+def bbp_serve_stats(plan: int) -> dict:
+    info = bbp_serve_info()
+    _check(_lib.bbp_serve_stats(plan, ctypes.byref(info)), "bbp_serve_stats")
+    return {name: getattr(info, name) for name, _ in bbp_serve_info._fields_}
 
 
 def bbp_plan_stats(plan: int) -> dict:

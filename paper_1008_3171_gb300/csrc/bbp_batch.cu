@@ -322,7 +322,6 @@ extern "C" bbp_status bbp_bits_batch(bbp_plan p, bbp_formula f, uint32_t count, 
   }
   BatchState* b = p->batch;
   // device buffers first (job descriptors hold accumulator addresses)
-  const unsigned long long* old_accum = b->d_accum;
   if (!grow_device(&b->d_accum, &b->c_accum, static_cast<size_t>(count) * kMaxLimbs) ||
       !grow_device(&b->d_queries, &b->c_queries, count) || !grow_device(&b->d_jobs_left, &b->c_jobs_left, count) ||
       !grow_device(&b->d_out, &b->c_out, static_cast<size_t>(count) * kOutStride) ||
@@ -332,7 +331,6 @@ extern "C" bbp_status bbp_bits_batch(bbp_plan p, bbp_formula f, uint32_t count, 
     return BBP_ENOMEM;
   if (!grow_device(&b->d_cursors, &b->c_cursors, static_cast<size_t>(kMaxWaves) * (kVariants + 1)))
     return BBP_ENOMEM;
-  (void)old_accum;
   BatchPlan bp;
   bbp_status st = plan_batch(p, f, count, n, P, b, &bp);
   if (st != BBP_OK) return st;

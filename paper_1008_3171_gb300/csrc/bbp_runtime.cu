@@ -128,6 +128,7 @@ bbp_status bbp_plan_create(bbp_plan* out, const bbp_plan_opts* opts) {
 bbp_status bbp_plan_destroy(bbp_plan p) {
   if (!p) return BBP_OK;
   cudaSetDevice(p->device);
+  release_serve_state(p);
   if (p->stream) cudaStreamSynchronize(p->stream);
   release_batch_state(p);
   cudaFree(p->d_slots);

@@ -31,8 +31,9 @@ struct bbp_plan_s {
   void* h_stage = nullptr;  // 4 KiB pinned staging
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bbp_stats stats{};
-  // batched / serving state (bbp_batch.cu)
+  // batched state (bbp_batch.cu) and serving engine (bbp_serve.cu)
   struct BatchState* batch = nullptr;
+  struct ServeEngine* serve = nullptr;
 };
 
 namespace bbp {
@@ -44,5 +45,6 @@ bbp_status launch_ranges(bbp_plan p, int f, uint64_t n, uint32_t W, const std::v
                          unsigned long long* slots, cudaStream_t st);
 void load_tune_table(bbp_plan p, const char* path);
 void release_batch_state(bbp_plan p);
+void release_serve_state(bbp_plan p);
 
 }  // namespace bbp

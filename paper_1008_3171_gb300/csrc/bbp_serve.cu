@@ -1,0 +1,595 @@
+// Serving: continuous batching of bit-position queries (bbp_submit / bbp_poll).
+//
+// An engine thread owns a pool of device accumulator slots (admission is by free
+// slots, i.e. by accumulator memory) and runs iterations.  Each iteration takes
+// from every active query a piece of its remaining work -- at most a fair share of
+// an iteration budget sized to a target duration from the measured throughput --
+// so a long query is sliced over many iterations while short queries that arrive
+// meanwhile join the next iteration and finish in one or two.  The pieces of an
+// iteration are head-term ranges and tails of different queries, consumed by the
+// same persistent queue kernels as a batch; each query's partial sums stay in its
+// slot between iterations.  A query's job counter carries one extra hold while it
+// has work left, so the device finalizes it (bits, certified count) exactly in the
+// iteration that runs its last piece; the host then publishes the result to
+// bbp_poll and frees the slot.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstdint>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "bbp.h"
+#include "bbp_kernels.cuh"
+#include "bbp_planner.h"
+#include "bbp_runtime.h"
+
+using namespace bbp;
+
+namespace {
+
+constexpr int kLmaxClasses[] = {3, 4, 6, 10, 16, 40};
+constexpr int kVariants = 6 * 3;
+constexpr uint32_t kOutStride = kMaxWorkingBits / 8;
+constexpr double kIterTargetSeconds = 0.025;  // target duration of one iteration
+constexpr double kInitialRate = 2.0e10;       // terms/s before the first measurement
+
+int lmax_index(int lmax) {
+  for (int i = 0; i < 6; ++i)
+    if (kLmaxClasses[i] == lmax) return i;
+  return -1;
+}
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+template <typename T>
+bool grow_dev(T** p, size_t* cap, size_t want) {
+  if (*cap >= want && *p) return true;
+  cudaFree(*p);
+  *p = nullptr;
+  const size_t n = std::max<size_t>(want, 1) * 2;
+  if (cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T)) != cudaSuccess) {
+    *cap = 0;
+    return false;
+  }
+  *cap = n;
+  return true;
+}
+
+template <typename T>
+bool grow_pinned(T** p, size_t* cap, size_t want) {
+  if (*cap >= want && *p) return true;
+  cudaFreeHost(*p);
+  *p = nullptr;
+  const size_t n = std::max<size_t>(want, 1) * 2;
+  if (cudaMallocHost(reinterpret_cast<void**>(p), n * sizeof(T)) != cudaSuccess) {
+    *cap = 0;
+    return false;
+  }
+  *cap = n;
+  return true;
+}
+
+// A query's work: head ranges (HeadArgs without `slots`, with their tile count and
+// kernel variant) and tail ranges, taken in order.
+struct Work {
+  bool tail;
+  int variant;
+  uint64_t tiles;  // head: warp tiles of the range
+  HeadArgs head;
+  TailArgs tailargs;
+};
+
+enum State { kPending = 0, kActive = 1, kDone = 2, kFailed = 3 };
+
+struct Query {
+  uint64_t ticket = 0;
+  uint64_t n = 0;
+  uint32_t P = 0, W = 0, L = 0;
+  int slot = -1;
+  int state = kPending;
+  bbp_status error = BBP_OK;
+  std::vector<Work> work;
+  size_t next = 0;         // next work item
+  uint64_t tile_off = 0;   // tiles of work[next] already handed out
+  uint64_t bound = 0;      // N + J + 1
+  uint64_t total_terms = 0;
+  bool final_in_flight = false;
+  std::vector<uint8_t> out;
+  uint32_t valid = 0;
+};
+
+}  // namespace
+
+struct ServeEngine {
+  bbp_plan plan = nullptr;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::thread thread;
+  bool stop = false;
+  bool started = false;
+  uint64_t next_ticket = 1;
+  std::deque<Query*> pending;
+  std::vector<Query*> active;
+  std::unordered_map<uint64_t, Query*> tickets;
+  std::vector<int> free_slots;
+  uint32_t max_slots = 0;
+  double rate = kInitialRate;  // measured terms/s
+  // device state
+  cudaStream_t stream = nullptr;
+  unsigned long long* d_accum = nullptr;
+  QueryDesc* d_queries = nullptr;
+  unsigned int* d_jobs_left = nullptr;
+  uint8_t* d_out = nullptr;
+  uint32_t* d_valid = nullptr;
+  unsigned long long* d_done = nullptr;
+  unsigned int* d_cursors = nullptr;
+  HeadArgs* d_jobs = nullptr;            size_t c_jobs = 0;
+  uint32_t* d_job_query = nullptr;       size_t c_job_query = 0;
+  uint64_t* d_job_tiles = nullptr;       size_t c_job_tiles = 0;
+  unsigned long long* d_job_ctr = nullptr; size_t c_job_ctr = 0;
+  TailArgs* d_tails = nullptr;           size_t c_tails = 0;
+  uint32_t* d_tail_query = nullptr;      size_t c_tail_query = 0;
+  HeadArgs* h_jobs = nullptr;            size_t hc_jobs = 0;
+  uint32_t* h_job_query = nullptr;       size_t hc_job_query = 0;
+  uint64_t* h_job_tiles = nullptr;       size_t hc_job_tiles = 0;
+  TailArgs* h_tails = nullptr;           size_t hc_tails = 0;
+  uint32_t* h_tail_query = nullptr;      size_t hc_tail_query = 0;
+  QueryDesc* h_queries = nullptr;
+  unsigned int* h_jobs_left = nullptr;
+  uint8_t* h_out = nullptr;
+  uint32_t* h_valid = nullptr;
+  // statistics
+  uint64_t iterations = 0;
+  uint64_t terms_done = 0;
+};
+
+namespace {
+
+// Host planning of one query into work items (the same ranges as bbp_bits).
+bbp_status plan_query_work(bbp_plan p, uint64_t n, uint32_t P, Query* q) {
+  uint32_t W;
+  if (n == 0 || !working_bits(P, p->guard, &W)) return BBP_EINVAL;
+  const uint32_t L = W / 32;
+  const int lmax = head_lmax_for(static_cast<int>(L));
+  if (lmax == 0) return BBP_EINVAL;
+  const FormulaDef& F = formula_def(BBP_BELLARD);
+  std::vector<TermRange> ranges;
+  uint64_t N = 0;
+  for (uint32_t j = 0; j < F.count; ++j) {
+    const int st = plan_series(F, j, n, W, static_cast<uint32_t>(lmax), 0, UINT64_MAX, ranges);
+    if (st == -6) return BBP_ERANGE;
+    if (st != 0) return BBP_EINVAL;
+    N += natural_end(F, j, n - 1, W);
+  }
+  const uint64_t tile = 32ull * p->streams * p->run;
+  q->n = n;
+  q->P = P;
+  q->W = W;
+  q->L = L;
+  q->bound = N + F.count + 1;
+  for (const TermRange& r : ranges) {
+    const SeriesDef& s = F.s[r.j];
+    Work w{};
+    w.tail = r.tail != 0;
+    q->total_terms += r.count;
+    if (w.tail) {
+      TailArgs& a = w.tailargs;
+      a.d = n - 1;
+      a.k_begin = r.k_begin;
+      a.count = r.count;
+      a.a = s.a;
+      a.b = s.b;
+      a.c = s.c;
+      a.step = F.step;
+      a.W = W;
+      a.L = L;
+      a.alternating = F.alternating;
+      a.negate = s.sign < 0 ? 1u : 0u;
+    } else {
+      HeadArgs& a = w.head;
+      a.d = n - 1;
+      a.k_begin = r.k_begin;
+      a.count = r.count;
+      a.a = s.a;
+      a.b = s.b;
+      a.c = s.c;
+      a.step = F.step;
+      a.W = W;
+      a.L = L;
+      a.alternating = F.alternating;
+      a.negate = s.sign < 0 ? 1u : 0u;  // the parity of the piece's first k is applied per piece
+      a.run = static_cast<uint32_t>(p->run);
+      a.window = r.window;
+      a.first = r.first;
+      w.tiles = (r.count + tile - 1) / tile;
+      w.variant = lmax_index(lmax) * 3 + r.path;
+    }
+    q->work.push_back(w);
+  }
+  if (q->work.empty()) {  // nothing to sum: a zero-length tail still retires the query
+    Work w{};
+    w.tail = true;
+    w.tailargs.W = W;
+    w.tailargs.L = L;
+    q->work.push_back(w);
+  }
+  return BBP_OK;
+}
+
+struct Piece {
+  bool tail;
+  int variant;
+  uint64_t tiles;
+  HeadArgs head;
+  TailArgs tailargs;
+  uint32_t slot;
+};
+
+// Takes up to `budget_tiles` tiles (at least one item) of q's remaining work.
+void take_pieces(ServeEngine* E, Query* q, uint64_t budget_tiles, std::vector<Piece>& out, uint64_t* terms) {
+  bbp_plan p = E->plan;
+  const uint64_t tile = 32ull * p->streams * p->run;
+  const FormulaDef& F = formula_def(BBP_BELLARD);
+  unsigned long long* slots = E->d_accum + static_cast<uint64_t>(q->slot) * kMaxLimbs;
+  bool first = true;
+  while (q->next < q->work.size() && (first || budget_tiles > 0)) {
+    first = false;
+    Work& w = q->work[q->next];
+    Piece pc{};
+    pc.slot = static_cast<uint32_t>(q->slot);
+    pc.tail = w.tail;
+    if (w.tail) {
+      pc.tailargs = w.tailargs;
+      pc.tailargs.slots = slots;
+      *terms += w.tailargs.count;
+      budget_tiles = budget_tiles > 0 ? budget_tiles - 1 : 0;
+      ++q->next;
+      q->tile_off = 0;
+    } else {
+      const uint64_t avail = w.tiles - q->tile_off;
+      const uint64_t take = std::max<uint64_t>(1, std::min(avail, budget_tiles));
+      HeadArgs a = w.head;
+      a.k_begin = w.head.k_begin + q->tile_off * tile;
+      const uint64_t end = std::min(w.head.k_begin + w.head.count, a.k_begin + take * tile);
+      a.count = end - a.k_begin;
+      const bool neg_series = w.head.negate != 0;
+      a.negate = (neg_series != (F.alternating && (a.k_begin & 1ull))) ? 1u : 0u;
+      a.slots = slots;
+      pc.head = a;
+      pc.variant = w.variant;
+      pc.tiles = (a.count + tile - 1) / tile;
+      *terms += a.count;
+      budget_tiles = budget_tiles > take ? budget_tiles - take : 0;
+      q->tile_off += take;
+      if (q->tile_off >= w.tiles) {
+        ++q->next;
+        q->tile_off = 0;
+      }
+    }
+    out.push_back(pc);
+  }
+}
+
+bool alloc_engine(ServeEngine* E) {
+  const size_t S = E->max_slots;
+  bool ok = cudaStreamCreateWithFlags(&E->stream, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaMalloc(&E->d_accum, sizeof(unsigned long long) * kMaxLimbs * S) == cudaSuccess &&
+            cudaMalloc(&E->d_queries, sizeof(QueryDesc) * S) == cudaSuccess &&
+            cudaMalloc(&E->d_jobs_left, sizeof(unsigned int) * S) == cudaSuccess &&
+            cudaMalloc(&E->d_out, static_cast<size_t>(kOutStride) * S) == cudaSuccess &&
+            cudaMalloc(&E->d_valid, sizeof(uint32_t) * S) == cudaSuccess &&
+            cudaMalloc(&E->d_done, sizeof(unsigned long long) * S) == cudaSuccess &&
+            cudaMalloc(&E->d_cursors, sizeof(unsigned int) * (kVariants + 1)) == cudaSuccess &&
+            cudaMallocHost(&E->h_queries, sizeof(QueryDesc) * S) == cudaSuccess &&
+            cudaMallocHost(&E->h_jobs_left, sizeof(unsigned int) * S) == cudaSuccess &&
+            cudaMallocHost(&E->h_out, static_cast<size_t>(kOutStride) * S) == cudaSuccess &&
+            cudaMallocHost(&E->h_valid, sizeof(uint32_t) * S) == cudaSuccess;
+  return ok;
+}
+
+void free_engine(ServeEngine* E) {
+  if (E->stream) cudaStreamSynchronize(E->stream);
+  cudaFree(E->d_accum);
+  cudaFree(E->d_queries);
+  cudaFree(E->d_jobs_left);
+  cudaFree(E->d_out);
+  cudaFree(E->d_valid);
+  cudaFree(E->d_done);
+  cudaFree(E->d_cursors);
+  cudaFree(E->d_jobs);
+  cudaFree(E->d_job_query);
+  cudaFree(E->d_job_tiles);
+  cudaFree(E->d_job_ctr);
+  cudaFree(E->d_tails);
+  cudaFree(E->d_tail_query);
+  cudaFreeHost(E->h_jobs);
+  cudaFreeHost(E->h_job_query);
+  cudaFreeHost(E->h_job_tiles);
+  cudaFreeHost(E->h_tails);
+  cudaFreeHost(E->h_tail_query);
+  cudaFreeHost(E->h_queries);
+  cudaFreeHost(E->h_jobs_left);
+  cudaFreeHost(E->h_out);
+  cudaFreeHost(E->h_valid);
+  if (E->stream) cudaStreamDestroy(E->stream);
+}
+
+// One iteration over the active queries.  Returns false on a CUDA error (every
+// in-flight query is then failed with BBP_ECUDA).
+bool run_iteration(ServeEngine* E, std::vector<Query*>& batch, std::vector<int>& fresh_slots) {
+  bbp_plan p = E->plan;
+  const uint64_t tile = 32ull * p->streams * p->run;
+  const uint64_t budget_terms = static_cast<uint64_t>(E->rate * kIterTargetSeconds);
+  const uint64_t budget_tiles = std::max<uint64_t>(1, budget_terms / tile);
+  const uint64_t share = std::max<uint64_t>(1, budget_tiles / std::max<size_t>(1, batch.size()));
+  std::vector<Piece> pieces;
+  uint64_t terms = 0;
+  std::vector<uint32_t> npieces(batch.size(), 0);
+  for (size_t i = 0; i < batch.size(); ++i) {
+    Query* q = batch[i];
+    const size_t before = pieces.size();
+    take_pieces(E, q, share, pieces, &terms);
+    npieces[i] = static_cast<uint32_t>(pieces.size() - before);
+    q->final_in_flight = q->next >= q->work.size();
+  }
+  // group head pieces by variant, tails apart
+  std::vector<uint32_t> vb(kVariants + 1, 0);
+  std::vector<const Piece*> heads, tails;
+  for (int v = 0; v < kVariants; ++v) {
+    vb[v] = static_cast<uint32_t>(heads.size());
+    for (const Piece& pc : pieces)
+      if (!pc.tail && pc.variant == v) heads.push_back(&pc);
+  }
+  vb[kVariants] = static_cast<uint32_t>(heads.size());
+  for (const Piece& pc : pieces)
+    if (pc.tail) tails.push_back(&pc);
+  const size_t nh = heads.size(), nt = tails.size();
+  if (!grow_pinned(&E->h_jobs, &E->hc_jobs, nh) || !grow_pinned(&E->h_job_query, &E->hc_job_query, nh) ||
+      !grow_pinned(&E->h_job_tiles, &E->hc_job_tiles, nh) || !grow_pinned(&E->h_tails, &E->hc_tails, nt) ||
+      !grow_pinned(&E->h_tail_query, &E->hc_tail_query, nt) || !grow_dev(&E->d_jobs, &E->c_jobs, nh) ||
+      !grow_dev(&E->d_job_query, &E->c_job_query, nh) || !grow_dev(&E->d_job_tiles, &E->c_job_tiles, nh) ||
+      !grow_dev(&E->d_job_ctr, &E->c_job_ctr, 2 * nh) || !grow_dev(&E->d_tails, &E->c_tails, nt) ||
+      !grow_dev(&E->d_tail_query, &E->c_tail_query, nt))
+    return false;
+  for (size_t i = 0; i < nh; ++i) {
+    E->h_jobs[i] = heads[i]->head;
+    E->h_job_query[i] = heads[i]->slot;
+    E->h_job_tiles[i] = heads[i]->tiles;
+  }
+  for (size_t i = 0; i < nt; ++i) {
+    E->h_tails[i] = tails[i]->tailargs;
+    E->h_tail_query[i] = tails[i]->slot;
+  }
+  cudaStream_t s = E->stream;
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+  for (int slot : fresh_slots)
+    chk(cudaMemsetAsync(E->d_accum + static_cast<uint64_t>(slot) * kMaxLimbs, 0,
+                        sizeof(unsigned long long) * kMaxLimbs, s));
+  for (size_t i = 0; i < batch.size(); ++i) {
+    Query* q = batch[i];
+    QueryDesc& Q = E->h_queries[q->slot];
+    Q.bound = q->bound;
+    Q.P = q->P;
+    Q.L = q->L;
+    Q.out_offset = static_cast<uint32_t>(q->slot) * kOutStride;
+    E->h_jobs_left[q->slot] = npieces[i] + (q->final_in_flight ? 0u : 1u);  // hold while work remains
+    chk(cudaMemcpyAsync(E->d_queries + q->slot, &Q, sizeof(QueryDesc), cudaMemcpyHostToDevice, s));
+    chk(cudaMemcpyAsync(E->d_jobs_left + q->slot, &E->h_jobs_left[q->slot], sizeof(unsigned int),
+                        cudaMemcpyHostToDevice, s));
+  }
+  chk(cudaMemcpyAsync(E->d_jobs, E->h_jobs, sizeof(HeadArgs) * nh, cudaMemcpyHostToDevice, s));
+  chk(cudaMemcpyAsync(E->d_job_query, E->h_job_query, sizeof(uint32_t) * nh, cudaMemcpyHostToDevice, s));
+  chk(cudaMemcpyAsync(E->d_job_tiles, E->h_job_tiles, sizeof(uint64_t) * nh, cudaMemcpyHostToDevice, s));
+  chk(cudaMemcpyAsync(E->d_tails, E->h_tails, sizeof(TailArgs) * nt, cudaMemcpyHostToDevice, s));
+  chk(cudaMemcpyAsync(E->d_tail_query, E->h_tail_query, sizeof(uint32_t) * nt, cudaMemcpyHostToDevice, s));
+  chk(cudaMemsetAsync(E->d_job_ctr, 0, sizeof(unsigned long long) * 2 * std::max<size_t>(nh, 1), s));
+  chk(cudaMemsetAsync(E->d_cursors, 0, sizeof(unsigned int) * (kVariants + 1), s));
+  BatchDev dev{};
+  dev.jobs = E->d_jobs;
+  dev.job_query = E->d_job_query;
+  dev.job_tiles = E->d_job_tiles;
+  dev.job_taken = E->d_job_ctr;
+  dev.job_done = E->d_job_ctr + nh;
+  dev.tails = E->d_tails;
+  dev.tail_query = E->d_tail_query;
+  dev.grab = static_cast<uint32_t>(p->grab);
+  dev.queries = E->d_queries;
+  dev.accum = E->d_accum;
+  dev.jobs_left = E->d_jobs_left;
+  dev.out = E->d_out;
+  dev.valid = E->d_valid;
+  dev.done_ns = E->d_done;
+  const double t0 = now_s();
+  chk(launch_queue_tail(dev, 0, static_cast<uint32_t>(nt), E->d_cursors + kVariants, p->sm_count * 4, s));
+  for (int v = 0; v < kVariants; ++v) {
+    if (vb[v] == vb[v + 1]) continue;
+    const int lmax = kLmaxClasses[v / 3], path = v % 3;
+    const int blocks = queue_occupancy(path, p->streams, lmax) * p->sm_count;
+    chk(launch_queue(dev, vb[v], vb[v + 1], E->d_cursors + v, path, p->streams, lmax, blocks, s));
+  }
+  // results of the queries that finished in this iteration
+  for (Query* q : batch) {
+    if (!q->final_in_flight) continue;
+    chk(cudaMemcpyAsync(E->h_out + static_cast<size_t>(q->slot) * kOutStride,
+                        E->d_out + static_cast<size_t>(q->slot) * kOutStride, (q->P + 7) / 8, cudaMemcpyDeviceToHost, s));
+    chk(cudaMemcpyAsync(E->h_valid + q->slot, E->d_valid + q->slot, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  }
+  chk(cudaStreamSynchronize(s));
+  const double dt = now_s() - t0;
+  if (e != cudaSuccess) return false;
+  if (dt > 1e-4 && terms > 0) E->rate = 0.7 * E->rate + 0.3 * (static_cast<double>(terms) / dt);
+  E->iterations++;
+  E->terms_done += terms;
+  return true;
+}
+
+void engine_main(ServeEngine* E) {
+  cudaSetDevice(E->plan->device);
+  for (;;) {
+    std::vector<Query*> batch;
+    std::vector<int> fresh;
+    {
+      std::unique_lock<std::mutex> lock(E->mu);
+      E->cv.wait(lock, [&] { return E->stop || !E->pending.empty() || !E->active.empty(); });
+      if (E->stop) return;
+      while (!E->pending.empty() && !E->free_slots.empty()) {  // admission by free accumulator slots
+        Query* q = E->pending.front();
+        E->pending.pop_front();
+        q->slot = E->free_slots.back();
+        E->free_slots.pop_back();
+        q->state = kActive;
+        E->active.push_back(q);
+        fresh.push_back(q->slot);
+      }
+      batch = E->active;
+    }
+    const bool ok = run_iteration(E, batch, fresh);
+    std::lock_guard<std::mutex> lock(E->mu);
+    std::vector<Query*> still;
+    for (Query* q : E->active) {
+      if (!ok) {
+        q->state = kFailed;
+        q->error = BBP_ECUDA;
+      } else if (q->final_in_flight) {
+        q->out.assign(E->h_out + static_cast<size_t>(q->slot) * kOutStride,
+                      E->h_out + static_cast<size_t>(q->slot) * kOutStride + (q->P + 7) / 8);
+        q->valid = E->h_valid[q->slot];
+        q->state = kDone;
+      } else {
+        still.push_back(q);
+        continue;
+      }
+      E->free_slots.push_back(q->slot);
+      q->slot = -1;
+      q->work.clear();
+      q->work.shrink_to_fit();
+    }
+    E->active.swap(still);
+  }
+}
+
+ServeEngine* engine_of(bbp_plan p, bbp_status* st) {
+  *st = BBP_OK;
+  if (p->serve) return p->serve;
+  ServeEngine* E = new (std::nothrow) ServeEngine();
+  if (!E) {
+    *st = BBP_ENOMEM;
+    return nullptr;
+  }
+  E->plan = p;
+  const size_t per_slot = sizeof(unsigned long long) * kMaxLimbs + kOutStride + 64;
+  E->max_slots = static_cast<uint32_t>(std::max<size_t>(1, std::min<size_t>(p->max_slots, p->accum_budget / per_slot)));
+  cudaSetDevice(p->device);
+  if (!alloc_engine(E)) {
+    free_engine(E);
+    delete E;
+    *st = BBP_ENOMEM;
+    return nullptr;
+  }
+  for (int s = static_cast<int>(E->max_slots) - 1; s >= 0; --s) E->free_slots.push_back(s);
+  E->thread = std::thread(engine_main, E);
+  E->started = true;
+  p->serve = E;
+  return E;
+}
+
+}  // namespace
+
+namespace bbp {
+
+void release_serve_state(bbp_plan p) {
+  ServeEngine* E = p->serve;
+  if (!E) return;
+  {
+    std::lock_guard<std::mutex> lock(E->mu);
+    E->stop = true;
+  }
+  E->cv.notify_all();
+  if (E->thread.joinable()) E->thread.join();
+  for (auto& kv : E->tickets) delete kv.second;
+  free_engine(E);
+  delete E;
+  p->serve = nullptr;
+}
+
+}  // namespace bbp
+
+extern "C" {
+
+bbp_status bbp_submit(bbp_plan p, uint64_t n, uint32_t P, bbp_ticket* t) {
+  if (!p || !t) return BBP_EINVAL;
+  Query* q = new (std::nothrow) Query();
+  if (!q) return BBP_ENOMEM;
+  const bbp_status ps = plan_query_work(p, n, P, q);
+  if (ps != BBP_OK) {
+    delete q;
+    return ps;
+  }
+  bbp_status st;
+  ServeEngine* E = engine_of(p, &st);
+  if (!E) {
+    delete q;
+    return st;
+  }
+  {
+    std::lock_guard<std::mutex> lock(E->mu);
+    // admission: a query waits for a slot only while the queue is shorter than the pool
+    if (E->pending.size() >= E->max_slots) {
+      delete q;
+      return BBP_EBUSY;
+    }
+    q->ticket = E->next_ticket++;
+    E->tickets[q->ticket] = q;
+    E->pending.push_back(q);
+    *t = q->ticket;
+  }
+  E->cv.notify_all();
+  return BBP_OK;
+}
+
+bbp_status bbp_poll(bbp_plan p, bbp_ticket t, uint8_t* out, uint32_t* valid_bits) {
+  if (!p) return BBP_EINVAL;
+  ServeEngine* E = p->serve;
+  if (!E) return BBP_ENOTFOUND;
+  std::lock_guard<std::mutex> lock(E->mu);
+  auto it = E->tickets.find(t);
+  if (it == E->tickets.end()) return BBP_ENOTFOUND;
+  Query* q = it->second;
+  if (q->state == kPending || q->state == kActive) return BBP_PENDING;
+  const bbp_status st = q->state == kFailed ? q->error : BBP_OK;
+  if (st == BBP_OK) {
+    if (out) std::memcpy(out, q->out.data(), q->out.size());
+    if (valid_bits) *valid_bits = q->valid;
+  }
+  E->tickets.erase(it);
+  delete q;
+  return st;
+}
+
+bbp_status bbp_serve_stats(bbp_plan p, bbp_serve_info* info) {
+  if (!p || !info) return BBP_EINVAL;
+  std::memset(info, 0, sizeof(*info));
+  ServeEngine* E = p->serve;
+  if (!E) return BBP_OK;
+  std::lock_guard<std::mutex> lock(E->mu);
+  info->pending = E->pending.size();
+  info->active = E->active.size();
+  info->slots = E->max_slots;
+  info->iterations = E->iterations;
+  info->terms = E->terms_done;
+  info->terms_per_s = E->rate;
+  return BBP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,101 @@
+"""Serving (bbp_submit / bbp_poll): continuous batching returns, for every query,
+exactly the bits the query gets alone -- while other queries (a long one and many
+short ones arriving over time) share the GPU with it."""
+
+import random
+import time
+
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bbp():
+    import paper_1008_3171_gb300 as m
+
+    return m
+
+
+def wait_all(bbp, plan, tickets, timeout_s=180.0):
+    done = {}
+    t_end = time.time() + timeout_s
+    while len(done) < len(tickets) and time.time() < t_end:
+        for t, (n, P) in tickets.items():
+            if t in done:
+                continue
+            r = bbp.bbp_poll(plan.handle, t, P)
+            if r is not None:
+                done[t] = r
+        time.sleep(0.002)
+    assert len(done) == len(tickets), "serving did not finish in time"
+    return done
+
+
+def test_results_in_the_mix_equal_results_alone(bbp):
+    plan = bbp.Plan(device=0, guard_bits=64, max_slots=64)
+    try:
+        tickets = {}
+        long_n, long_P = 10**10 + 1, 256
+        tickets[bbp.bbp_submit(plan.handle, long_n, long_P)] = (long_n, long_P)
+        rng = random.Random(21)
+        arrivals = workloads.serving_arrivals(40, rate_per_s=200.0, seed=21, lo=2.0, hi=8.0)
+        t0 = time.time()
+        for t_arr, n, P in arrivals:
+            delay = t0 + t_arr - time.time()
+            if delay > 0:
+                time.sleep(delay)
+            t = bbp.bbp_submit(plan.handle, n, P)
+            assert t is not None
+            tickets[t] = (n, P)
+        done = wait_all(bbp, plan, tickets)
+        info = bbp.bbp_serve_stats(plan.handle)
+        assert info["iterations"] > 1 and info["pending"] == 0 and info["active"] == 0
+        alone = bbp.Plan(device=0, guard_bits=64)
+        try:
+            for t, (n, P) in tickets.items():
+                assert done[t] == alone.bits(n, P), (n, P)
+                if n < 10**7:
+                    assert done[t] == oracle.c_bits(n, P, 64), (n, P)
+        finally:
+            alone.close()
+        assert rng is not None
+    finally:
+        plan.close()
+
+
+def test_admission_is_bounded_by_the_slot_pool(bbp):
+    plan = bbp.Plan(device=0, guard_bits=64, max_slots=1)
+    try:
+        first = bbp.bbp_submit(plan.handle, 10**11 + 1, 64)
+        t_end = time.time() + 10
+        while bbp.bbp_serve_stats(plan.handle)["active"] != 1 and time.time() < t_end:
+            time.sleep(0.001)
+        second = bbp.bbp_submit(plan.handle, 1000, 64)   # waits for the one slot
+        assert second is not None
+        assert bbp.bbp_submit(plan.handle, 1001, 64) is None  # the queue is as long as the pool
+        done = wait_all(bbp, plan, {first: (10**11 + 1, 64), second: (1000, 64)})
+        assert done[second] == oracle.c_bits(1000, 64, 64)
+    finally:
+        plan.close()
+
+
+def test_tickets(bbp):
+    plan = bbp.Plan(device=0, guard_bits=32)
+    try:
+        with pytest.raises(bbp.BBPError) as e:
+            bbp.bbp_poll(plan.handle, 12345, 8)
+        assert e.value.status == bbp.BBP_ENOTFOUND
+        t = bbp.bbp_submit(plan.handle, 9, 8)
+        done = wait_all(bbp, plan, {t: (9, 8)})
+        assert done[t] == (0x3F, 8)
+        with pytest.raises(bbp.BBPError) as e:
+            bbp.bbp_poll(plan.handle, t, 8)
+        assert e.value.status == bbp.BBP_ENOTFOUND
+        with pytest.raises(bbp.BBPError):
+            bbp.bbp_submit(plan.handle, 0, 8)
+    finally:
+        plan.close()
