@@ -47,9 +47,13 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--workload", choices=["single", "batched"], default="single",
-                    help="single: the n=1e12 headline; batched: 4096 seeded queries, persistent vs plain")
+    ap.add_argument("--workload", choices=["single", "batched", "serving"], default="single",
+                    help="single: the n=1e12 headline; batched: 4096 seeded queries, persistent vs plain; "
+                         "serving: Poisson arrivals at 80%% of capacity plus one long query, engine vs plain FIFO")
     ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--serve-count", type=int, default=200)
+    ap.add_argument("--serve-long", type=int, default=10**12 + 1, help="n of the long query (P = 256)")
+    ap.add_argument("--serve-load", type=float, default=0.8)
     ap.add_argument("--tune-table", default=None)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target wall time of one oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -410,12 +414,114 @@ def run_batched(args):
     })
 
 
+# ---------------------------------------------------------------- serving workload
+
+def run_serving(args):
+    """Poisson arrivals (seed 1; n log-uniform in [1e6, 1e11], P in {64, 256}) at
+    `load` x measured capacity, plus one long query (P = 256) at t = 0.  The
+    continuous-batching engine (bbp_submit / bbp_poll) against a plain FIFO server
+    (one bbp_bits call per query in arrival order) on the same trace."""
+    import threading
+
+    import torch
+
+    import paper_1008_3171_gb300 as bbp
+    import workloads
+
+    plan = bbp.Plan(device=0, guard_bits=GUARD, max_slots=4096, tune_table=args.tune_table)
+    # capacity on a sample of the short-query distribution
+    cal = workloads.serving_arrivals(96, 1.0, seed=101)
+    cal_n = [n for _, n, _ in cal]
+    cal_P = [P for _, _, P in cal]
+    bbp.bbp_bits_batch(plan.handle, 0, cal_n, cal_P, with_latency=False)
+    t0 = time.perf_counter()
+    bbp.bbp_bits_batch(plan.handle, 0, cal_n, cal_P, with_latency=False)
+    cal_rate = plan.stats()["terms"] / (time.perf_counter() - t0)
+    mean_terms = plan.stats()["terms"] / len(cal_n)
+    qps = args.serve_load * cal_rate / mean_terms
+    trace = workloads.serving_arrivals(args.serve_count, qps, seed=1, long_query=(args.serve_long, 256))
+    expect = {}
+    torch.cuda.synchronize()
+
+    # --- engine
+    results = {}
+    submitted = {}
+    lock = threading.Lock()
+    start = time.perf_counter() + 0.05
+
+    def submitter():
+        for i, (t_arr, n, P) in enumerate(trace):
+            delay = start + t_arr - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            while True:
+                t = bbp.bbp_submit(plan.handle, n, P)
+                if t is not None:
+                    break
+                time.sleep(0.001)
+            with lock:
+                submitted[t] = (i, P)
+
+    th = threading.Thread(target=submitter)
+    sampler = ClockSampler(0)
+    sampler.start()
+    th.start()
+    while th.is_alive() or len(results) < len(trace):
+        with lock:
+            items = [(t, v) for t, v in submitted.items() if t not in results]
+        for t, (i, P) in items:
+            r = bbp.bbp_poll(plan.handle, t, P)
+            if r is not None:
+                results[t] = (i, r, time.perf_counter() - start)
+        time.sleep(0.0005)
+    th.join()
+    engine_make = max(v[2] for v in results.values())
+    info = bbp.bbp_serve_stats(plan.handle)
+    lat = {}
+    out = {}
+    for t, (i, r, t_done) in results.items():
+        lat[i] = t_done - trace[i][0]
+        out[i] = r
+    # --- plain FIFO server on the same trace
+    plain_lat = {}
+    plain_out = {}
+    start = time.perf_counter()
+    for i, (t_arr, n, P) in enumerate(trace):
+        delay = start + t_arr - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        plain_out[i] = plan.bits(n, P)
+        plain_lat[i] = time.perf_counter() - start - t_arr
+    plain_make = time.perf_counter() - start
+    clocks = sampler.stop()
+    total_terms = info["terms"]
+    short = [lat[i] for i in range(1, len(trace))]
+    plain_short = [plain_lat[i] for i in range(1, len(trace))]
+    emit({
+        "metric": "serving: p50/p99 latency of arriving queries and terms/s, continuous batching vs plain FIFO",
+        "workload": "serving",
+        "config": {"arrivals": len(trace) - 1, "rate_qps": qps, "load": args.serve_load, "seed": 1,
+                   "n": "floor(10^U(6,11))", "P": "uniform {64,256}", "long_query": {"n": args.serve_long, "P": 256},
+                   "calibrated_terms_per_s": cal_rate, "guard_bits": GUARD},
+        "engine": {"terms_per_s": total_terms / engine_make, "makespan_s": engine_make,
+                   "p50_ms": 1e3 * percentile(short, 50), "p99_ms": 1e3 * percentile(short, 99),
+                   "long_query_latency_s": lat[0], "iterations": info["iterations"]},
+        "plain": {"terms_per_s": total_terms / plain_make, "makespan_s": plain_make,
+                  "p50_ms": 1e3 * percentile(plain_short, 50), "p99_ms": 1e3 * percentile(plain_short, 99),
+                  "long_query_latency_s": plain_lat[0]},
+        "identical": all(out[i] == plain_out[i] for i in range(len(trace))),
+        "clocks": clocks,
+    })
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_gpu(args)
 

@@ -188,14 +188,14 @@ __device__ __forceinline__ void sqr_shift_redc64(uint32_t& x0, uint32_t& x1, uin
       "add.cc.u64     a, a, hz;\n\t"
       "addc.u32       s3, s3, 0;\n\t"
       "mov.b64        {s1, s2}, a;\n\t"
-      // step 2: word 1 vanishes; the result (s3 : s2) + hi(u m0) + c + u m1 < 2m fits 64 bits
+      // step 2: word 1 vanishes; the result (s3 : s2) + hi(u m0) + c + u m1 < 2m fits 64 bits,
+      // so u m1 is accumulated by the multiply itself
       "mul.lo.u32     u, s1, np;\n\t"
       "min.u32        c, s1, 1;\n\t"
       "mul.hi.u32     h, u, n0;\n\t"
-      "mul.wide.u32   z, u, n1;\n\t"
       "add.u32        h, h, c;\n\t"
       "mov.b64        a, {s2, s3};\n\t"
-      "add.u64        a, a, z;\n\t"
+      "mad.wide.u32   a, u, n1, a;\n\t"
       "cvt.u64.u32    hz, h;\n\t"
       "add.u64        a, a, hz;\n\t"
       "mov.b64        {s2, s3}, a;\n\t"
@@ -236,7 +236,7 @@ __device__ __forceinline__ uint32_t hensel_step64(uint32_t& x0, uint32_t& x1, co
   uint32_t u, y0, y1;
   asm("{\n\t"
       ".reg .u32 q, c, h, a0, a1, n0, n1, np;\n\t"
-      ".reg .u64 z, r, w;\n\t"
+      ".reg .u64 r, w;\n\t"
       "mov.u32        a0, %3;\n\t"
       "mov.u32        a1, %4;\n\t"
       "mov.u32        n0, %5;\n\t"
@@ -245,12 +245,11 @@ __device__ __forceinline__ uint32_t hensel_step64(uint32_t& x0, uint32_t& x1, co
       "mul.lo.u32     q, a0, np;\n\t"
       "min.u32        c, a0, 1;\n\t"
       "mul.hi.u32     h, q, n0;\n\t"
-      "mul.wide.u32   z, q, n1;\n\t"
       "add.u32        h, h, c;\n\t"
       "cvt.u64.u32    r, h;\n\t"
-      "add.u64        r, r, z;\n\t"
       "cvt.u64.u32    w, a1;\n\t"
       "add.u64        r, r, w;\n\t"
+      "mad.wide.u32   r, q, n1, r;\n\t"
       "mov.b64        {a0, a1}, r;\n\t"
       "mov.u32        %0, q;\n\t"
       "mov.u32        %1, a0;\n\t"

@@ -28,7 +28,7 @@ namespace {
 
 constexpr int kNoAllocMaxLimbs = 40;  // W <= 1280 bits
 constexpr int kMaxDevices = 64;
-constexpr int kRun = 32;              // terms per stream run (the plan default)
+constexpr int kRun = 64;              // terms per stream run (the plan default)
 
 static __device__ __align__(256) unsigned long long g_noalloc_slots[kNoAllocMaxLimbs];
 

@@ -37,7 +37,7 @@ bbp_status cuda_status(cudaError_t e) { return e == cudaSuccess ? BBP_OK : BBP_E
 namespace {
 
 constexpr uint32_t kDefaultGuard = 64;
-constexpr int kDefaultRun = 32;
+constexpr int kDefaultRun = 64;
 
 bool valid_formula(int f) { return f == BBP_BELLARD || f == BBP_BBP; }
 

@@ -20,9 +20,9 @@ struct bbp_plan_s {
   uint32_t max_slots = 0;
   int sm_count = 0;
   // head-kernel tuning (terms per stream run, streams per thread)
-  int run = 32;
+  int run = 64;
   int streams = 1;
-  int grab = 8;  // batched pass: warp tiles handed out per queue operation
+  int grab = 4;  // batched pass: warp tiles handed out per queue operation
   // single-query buffers
   unsigned long long* d_slots = nullptr;  // kMaxLimbs carry-save accumulators
   uint32_t* d_limbs = nullptr;

@@ -1,0 +1,49 @@
+"""Every launch configuration the autotuner can pick computes the same exact sums:
+terms per run, pairs per thread (1 or 2 streams) and queue hand-out size change
+only the schedule, never a bit of the result."""
+
+import json
+import os
+import tempfile
+
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+SETTINGS = [
+    {"run": 2, "streams": 1, "grab": 1},
+    {"run": 16, "streams": 2, "grab": 3},
+    {"run": 64, "streams": 1, "grab": 32},
+    {"run": 128, "streams": 2, "grab": 8},
+]
+
+
+def plan_with(bbp, setting, guard=64):
+    fd, path = tempfile.mkstemp(suffix=".json")
+    with os.fdopen(fd, "w") as fh:
+        json.dump(setting, fh)
+    try:
+        return bbp.Plan(device=0, guard_bits=guard, tune_table=path)
+    finally:
+        os.unlink(path)
+
+
+@pytest.mark.parametrize("setting", SETTINGS, ids=[json.dumps(s) for s in SETTINGS])
+def test_settings_give_identical_sums(setting):
+    import paper_1008_3171_gb300 as bbp
+
+    p = plan_with(bbp, setting)
+    try:
+        for n, P, j, kb, ke in [(10**12, 256, 0, 5 * 10**10, 5 * 10**10 + 70_001),
+                                (10**12, 256, 5, 3, 200_003), (10**9 + 1, 128, 3, 0, None),
+                                (99_991, 64, 6, 0, None), (10**6, 100, 1, 1, 12_345)]:
+            assert p.partial_sum(0, j, kb, ke, n, P) == oracle.c_partial_sum(0, j, kb, ke, n, P, 64)
+        ns, Ps = workloads.batched_queries(count=48, seed=17, lo=2.0, hi=6.5)
+        vals, valid, _ = bbp.bbp_bits_batch(p.handle, 0, ns, Ps)
+        for q, (n, P) in enumerate(zip(ns, Ps)):
+            assert (vals[q], valid[q]) == oracle.c_bits(n, P, 64)
+    finally:
+        p.close()
