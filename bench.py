@@ -212,6 +212,26 @@ def expected_bits_check(bits_value: int, valid: int) -> bool:
     return valid == P_BITS and (bits_value & ((1 << 255) - 1)) == ref >> (row["bits"] - 255)
 
 
+def head_kernel_traffic():
+    """DRAM bytes per head-kernel launch from the committed ncu capture, if the
+    kernel sources are still the ones that capture measured (else None)."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "head_kernel_traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+        h = hashlib.sha256()
+        for f in rec["kernel_sources"]:
+            with open(os.path.join(ROOT, f), "rb") as src:
+                h.update(src.read())
+        if h.hexdigest() == rec["kernel_sources_sha256"]:
+            return rec["dram_bytes_per_launch"]
+    except (OSError, KeyError, ValueError):
+        pass
+    return None
+
+
 def run_gpu(args):
     import torch
 
@@ -341,7 +361,7 @@ def run_gpu(args):
                 "note": "bbp_bits with host output; the query (n, P) travels as kernel arguments"},
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T IMAD/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak) if achieved else None, "traffic": head_kernel_traffic(),
                      "kernel": "head_kernel", "head_launches": head_launches,
                      "peak_basis": f"{sms} SMs x {IMAD_LANES_PER_CLK_PER_SM} IMAD lanes/clk x {max_mhz:.0f} MHz"},
         "cpu_baseline": cpu,
