@@ -125,12 +125,7 @@ __device__ __forceinline__ void process_tile(const HeadArgs& A, const uint64_t t
       }
     }
     const int nb = static_cast<int>(__reduce_max_sync(0xffffffffu, static_cast<uint32_t>(nbl)));
-    // A 4-bit first window (path 1, moduli below 2^40) leaves x < m 2^15: its first
-    // squaring takes the general routine (x < 65 m afterwards) and needs two more
-    // squarings in the same group before the next shift, so at least 3 bits remain.
-    const int first = static_cast<int>(A.first);
-    const int h = nb > 0 ? max(0, min(first, nb - (first == 4 ? 3 : 1))) : 0;
-    const bool first_general = SMALL && first == 4 && h == 4;
+    const int h = nb > 0 ? min(static_cast<int>(A.first), nb - 1) : 0;
     const int low = nb - h;  // bits left after the first window
     uint64_t rem[NT];
 #pragma unroll
@@ -150,17 +145,6 @@ __device__ __forceinline__ void process_tile(const HeadArgs& A, const uint64_t t
     // len - 1 plain squarings, then one squaring with the group's value shifted in
     const uint32_t zero[NT] = {};
     int p = low;
-    if (first_general) {  // the first group, len >= 3: general, plain..., shifted
-      const int len = min(window, p);
-      p -= len;
-      square_all<WIDE, false, NT>(x0, x1, m0, m1, mp, zero, false);
-      if (len == 4) square_all<WIDE, SMALL, NT>(x0, x1, m0, m1, mp, zero, false);
-      square_all<WIDE, SMALL, NT>(x0, x1, m0, m1, mp, zero, false);
-      uint32_t sh[NT];
-#pragma unroll
-      for (int t = 0; t < NT; ++t) sh[t] = static_cast<uint32_t>(rem[t] >> p) & ((1u << len) - 1u);
-      square_all<WIDE, SMALL, NT>(x0, x1, m0, m1, mp, sh, true);
-    }
     while (p > 0) {
       const int len = min(window, p);
       p -= len;

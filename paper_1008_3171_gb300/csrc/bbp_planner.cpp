@@ -64,11 +64,10 @@ uint64_t natural_end(const FormulaDef& f, uint32_t j, uint64_t d, uint32_t W) {
   }
 }
 
-void window_params(int path, int lbits, uint8_t* window, uint8_t* first, bool big_first) {
+void window_params(int path, int lbits, uint8_t* window, uint8_t* first) {
   // shifted reduction keeps x < 2m while lbits + s <= 61 (64-bit) / <= 30 (32-bit);
   // the first window (x = (R mod m) << w0) needs lbits + 2 w0 + 1 <= 64 / 32, and on
-  // path 1 also x < 2^48 (x1^2 < 2^32), i.e. lbits + w0 <= 48 -- except for the
-  // 4-bit first window below.
+  // path 1 also x < 2^48 (x1^2 < 2^32), i.e. lbits + w0 <= 48.
   const bool wide = path > 0;
   const int shift_cap = wide ? 61 - lbits : 30 - lbits;
   const int rbits = wide ? 64 : 32;
@@ -78,10 +77,6 @@ void window_params(int path, int lbits, uint8_t* window, uint8_t* first, bool bi
   while (h < 4 && lbits + 2 * ((1 << (h + 1)) - 1) + 1 <= rbits &&
          (path != 1 || lbits + (1 << (h + 1)) - 1 <= 48))
     ++h;
-  // path 1, moduli below 2^40: a 4-bit first window, whose first squaring the kernel
-  // does with the general routine (x < m 2^15 < 2^55 before it, < 65 m after it,
-  // < 2m after one more plain squaring; the first group then has >= 3 squarings)
-  if (big_first && path == 1 && lbits <= 40 && w >= 3) h = 4;
   *window = static_cast<uint8_t>(w);
   *first = static_cast<uint8_t>(h);
 }
@@ -89,7 +84,7 @@ void window_params(int path, int lbits, uint8_t* window, uint8_t* first, bool bi
 int path_for_bits(int lbits) { return lbits < kWideMinBits ? 0 : (lbits <= kSmallMaxBits ? 1 : 2); }
 
 double head_term_imad(int path, int nb, int first, int lmax) {
-  const int h = nb > 0 ? std::max(0, std::min(first, nb - (first == 4 ? 3 : 1))) : 0;
+  const int h = nb > 0 ? std::min(first, nb - 1) : 0;
   const int sq = nb - h;
   if (path == 0) return 4.0 * sq + 2.0 * lmax + 8.0;
   return (path == 1 ? 13.0 : 14.0) * sq + 4.0 * lmax + 8.0;
@@ -128,7 +123,7 @@ double range_imad(const FormulaDef& f, const SeriesDef& s, uint64_t d, uint32_t 
 }  // namespace
 
 int plan_series(const FormulaDef& f, uint32_t j, uint64_t n, uint32_t W, uint32_t lmax, uint64_t k_lo,
-                uint64_t k_hi, std::vector<TermRange>& out, bool big_first) {
+                uint64_t k_hi, std::vector<TermRange>& out) {
   if (n == 0 || j >= f.count || W == 0 || W % 32 != 0 || W > kMaxWorkingBits) return -1;
   const SeriesDef& s = f.s[j];
   const uint64_t d = n - 1;
@@ -152,7 +147,7 @@ int plan_series(const FormulaDef& f, uint32_t j, uint64_t n, uint32_t W, uint32_
       if (k0 >= k1) continue;
       const int path = path_for_bits(l);
       uint8_t w, h;
-      window_params(path, l, &w, &h, big_first);
+      window_params(path, l, &w, &h);
       if (!groups.empty() && groups.back().path == path && groups.back().w == w && groups.back().h == h &&
           groups.back().k1 == k0) {
         groups.back().k1 = k1;

@@ -53,7 +53,7 @@ uint64_t natural_end(const FormulaDef& f, uint32_t j, uint64_t d, uint32_t W);
 int path_for_bits(int lbits);
 
 // Ladder parameters for moduli of at most `lbits` bits on the given path.
-void window_params(int path, int lbits, uint8_t* window, uint8_t* first, bool big_first = true);
+void window_params(int path, int lbits, uint8_t* window, uint8_t* first);
 
 // Algorithmic work of one head term whose ladder exponent has nb bits, counted as
 // 32-bit halves of 32x32-bit products (the low or high word of a product; a full
@@ -72,6 +72,6 @@ void shard_range(const FormulaDef& f, uint32_t j, uint64_t n, uint32_t W, uint32
 // Appends the ranges of series j restricted to k in [k_lo, k_hi) (k_hi = UINT64_MAX:
 // natural end).  Returns 0, or -6 (modulus too large) / -1 (bad argument).
 int plan_series(const FormulaDef& f, uint32_t j, uint64_t n, uint32_t W, uint32_t lmax, uint64_t k_lo,
-                uint64_t k_hi, std::vector<TermRange>& out, bool big_first = true);
+                uint64_t k_hi, std::vector<TermRange>& out);
 
 }  // namespace bbp

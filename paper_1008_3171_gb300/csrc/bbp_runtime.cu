@@ -242,13 +242,13 @@ bbp_status launch_ranges(bbp_plan p, int f, uint64_t n, uint32_t W, const std::v
 }
 
 bbp_status plan_query(int f, uint64_t n, uint32_t W, int j_only, uint64_t k_lo, uint64_t k_hi,
-                      std::vector<TermRange>& ranges, uint64_t* n_terms, bool big_first) {
+                      std::vector<TermRange>& ranges, uint64_t* n_terms) {
   const FormulaDef& F = formula_def(f);
   const int lmax = head_lmax_for(static_cast<int>(W / 32));
   uint64_t N = 0;
   for (uint32_t j = 0; j < F.count; ++j) {
     if (j_only >= 0 && static_cast<int>(j) != j_only) continue;
-    const int st = plan_series(F, j, n, W, static_cast<uint32_t>(lmax), k_lo, k_hi, ranges, big_first);
+    const int st = plan_series(F, j, n, W, static_cast<uint32_t>(lmax), k_lo, k_hi, ranges);
     if (st == -6) return BBP_ERANGE;
     if (st != 0) return BBP_EINVAL;
     N += natural_end(F, j, n - 1, W);
@@ -268,8 +268,7 @@ bbp_status bbp_partial_sum_async(bbp_plan p, bbp_formula f, uint32_t denominator
   uint32_t W;
   if (!working_bits(P, p->guard, &W)) return BBP_EINVAL;
   std::vector<TermRange> ranges;
-  const bbp_status st =
-      plan_query(f, n, W, static_cast<int>(denominator), k_begin, k_end, ranges, nullptr, p->big_first);
+  const bbp_status st = plan_query(f, n, W, static_cast<int>(denominator), k_begin, k_end, ranges, nullptr);
   if (st != BBP_OK) return st;
   BBP_CUDA(cudaSetDevice(p->device));
   cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : p->stream;
@@ -301,7 +300,7 @@ bbp_status bbp_bits_async(bbp_plan p, bbp_formula f, uint64_t n, uint32_t P, uin
   if (!working_bits(P, p->guard, &W)) return BBP_EINVAL;
   std::vector<TermRange> ranges;
   uint64_t N = 0;
-  const bbp_status st = plan_query(f, n, W, -1, 0, UINT64_MAX, ranges, &N, p->big_first);
+  const bbp_status st = plan_query(f, n, W, -1, 0, UINT64_MAX, ranges, &N);
   if (st != BBP_OK) return st;
   BBP_CUDA(cudaSetDevice(p->device));
   cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : p->stream;
@@ -338,7 +337,7 @@ bbp_status bbp_accumulate_async(bbp_plan p, bbp_formula f, uint64_t n, uint32_t 
   for (uint32_t j = 0; j < F.count; ++j) {
     uint64_t kb, ke;
     shard_range(F, j, n, W, shard, nshards, &kb, &ke);
-    const bbp_status st = plan_query(f, n, W, static_cast<int>(j), kb, ke, ranges, nullptr, p->big_first);
+    const bbp_status st = plan_query(f, n, W, static_cast<int>(j), kb, ke, ranges, nullptr);
     if (st != BBP_OK) return st;
   }
   BBP_CUDA(cudaSetDevice(p->device));

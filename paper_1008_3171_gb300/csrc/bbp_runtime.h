@@ -23,7 +23,6 @@ struct bbp_plan_s {
   int run = 64;
   int streams = 1;
   int grab = 4;  // batched pass: warp tiles handed out per queue operation
-  bool big_first = true;  // 4-bit first window on the 47-bit path (moduli below 2^40)
   // single-query buffers
   unsigned long long* d_slots = nullptr;  // kMaxLimbs carry-save accumulators
   uint32_t* d_limbs = nullptr;
@@ -41,7 +40,7 @@ namespace bbp {
 
 bbp_status cuda_status(cudaError_t e);
 bbp_status plan_query(int f, uint64_t n, uint32_t W, int j_only, uint64_t k_lo, uint64_t k_hi,
-                      std::vector<TermRange>& ranges, uint64_t* n_terms, bool big_first = true);
+                      std::vector<TermRange>& ranges, uint64_t* n_terms);
 bbp_status launch_ranges(bbp_plan p, int f, uint64_t n, uint32_t W, const std::vector<TermRange>& ranges,
                          unsigned long long* slots, cudaStream_t st);
 void load_tune_table(bbp_plan p, const char* path);

@@ -1,5 +1,5 @@
 // Autotune table loading: a small JSON object written by the autotuner
-// (paper_1008_3171_gb300/autotune.py), e.g. {"run": 64, "streams": 1, "grab": 4, "big_first": 1}.
+// (paper_1008_3171_gb300/autotune.py), e.g. {"run": 32, "streams": 1, "grab": 8}.
 // Unknown keys are ignored; missing keys keep the built-in defaults.
 #include <cstdio>
 #include <cstdlib>
@@ -37,7 +37,6 @@ void load_tune_table(bbp_plan p, const char* path) {
   if (read_int(text, "run", &v) && v >= 2 && v <= 4096 && v % 2 == 0) p->run = static_cast<int>(v);
   if (read_int(text, "streams", &v) && (v == 1 || v == 2)) p->streams = static_cast<int>(v);
   if (read_int(text, "grab", &v) && v >= 1 && v <= 1024) p->grab = static_cast<int>(v);
-  if (read_int(text, "big_first", &v) && (v == 0 || v == 1)) p->big_first = v == 1;
 }
 
 }  // namespace bbp
