@@ -11,11 +11,13 @@
 // slot between iterations.  A query's job counter carries one extra hold while it
 // has work left, so the device finalizes it (bits, certified count) exactly in the
 // iteration that runs its last piece; the host then publishes the result to
-// bbp_poll and frees the slot.
+// bbp_poll and frees the slot.  Iterations run one at a time: a query that
+// arrives while one runs joins the next.  (Planning iteration i+1 while i runs was
+// measured on the serving workload: the same terms/s, and every arrival waits one
+// iteration longer, so the median latency rose from 46 to 72 ms.)
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <chrono>
 #include <condition_variable>
 #include <cstdint>
 #include <cstring>
@@ -45,10 +47,6 @@ int lmax_index(int lmax) {
   for (int i = 0; i < 6; ++i)
     if (kLmaxClasses[i] == lmax) return i;
   return -1;
-}
-
-double now_s() {
-  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
 template <typename T>
@@ -110,6 +108,24 @@ struct Query {
 
 }  // namespace
 
+// Pinned host staging of one iteration: what it uploads, what it downloads, and
+// the queries it finishes.
+struct HostStage {
+  HeadArgs* jobs = nullptr;          size_t c_jobs = 0;
+  uint32_t* job_query = nullptr;     size_t c_job_query = 0;
+  uint64_t* job_tiles = nullptr;     size_t c_job_tiles = 0;
+  TailArgs* tails = nullptr;         size_t c_tails = 0;
+  uint32_t* tail_query = nullptr;    size_t c_tail_query = 0;
+  QueryDesc* queries = nullptr;      // one per slot
+  unsigned int* jobs_left = nullptr; // one per slot
+  uint8_t* out = nullptr;            // kOutStride bytes per slot
+  uint32_t* valid = nullptr;         // one per slot
+  cudaEvent_t start = nullptr, done = nullptr;
+  std::vector<Query*> finishing;     // queries whose last piece runs in this iteration
+  uint64_t terms = 0;
+  bool in_flight = false;
+};
+
 struct ServeEngine {
   bbp_plan plan = nullptr;
   std::mutex mu;
@@ -119,12 +135,12 @@ struct ServeEngine {
   bool started = false;
   uint64_t next_ticket = 1;
   std::deque<Query*> pending;
-  std::vector<Query*> active;
+  std::vector<Query*> active;        // admitted, with work left to hand out
   std::unordered_map<uint64_t, Query*> tickets;
   std::vector<int> free_slots;
   uint32_t max_slots = 0;
   double rate = kInitialRate;  // measured terms/s
-  // device state
+  // device state (shared by consecutive iterations: stream order separates them)
   cudaStream_t stream = nullptr;
   unsigned long long* d_accum = nullptr;
   QueryDesc* d_queries = nullptr;
@@ -139,15 +155,7 @@ struct ServeEngine {
   unsigned long long* d_job_ctr = nullptr; size_t c_job_ctr = 0;
   TailArgs* d_tails = nullptr;           size_t c_tails = 0;
   uint32_t* d_tail_query = nullptr;      size_t c_tail_query = 0;
-  HeadArgs* h_jobs = nullptr;            size_t hc_jobs = 0;
-  uint32_t* h_job_query = nullptr;       size_t hc_job_query = 0;
-  uint64_t* h_job_tiles = nullptr;       size_t hc_job_tiles = 0;
-  TailArgs* h_tails = nullptr;           size_t hc_tails = 0;
-  uint32_t* h_tail_query = nullptr;      size_t hc_tail_query = 0;
-  QueryDesc* h_queries = nullptr;
-  unsigned int* h_jobs_left = nullptr;
-  uint8_t* h_out = nullptr;
-  uint32_t* h_valid = nullptr;
+  HostStage stage;
   // statistics
   uint64_t iterations = 0;
   uint64_t terms_done = 0;
@@ -289,11 +297,19 @@ bool alloc_engine(ServeEngine* E) {
             cudaMalloc(&E->d_out, static_cast<size_t>(kOutStride) * S) == cudaSuccess &&
             cudaMalloc(&E->d_valid, sizeof(uint32_t) * S) == cudaSuccess &&
             cudaMalloc(&E->d_done, sizeof(unsigned long long) * S) == cudaSuccess &&
-            cudaMalloc(&E->d_cursors, sizeof(unsigned int) * (kVariants + 1)) == cudaSuccess &&
-            cudaMallocHost(&E->h_queries, sizeof(QueryDesc) * S) == cudaSuccess &&
-            cudaMallocHost(&E->h_jobs_left, sizeof(unsigned int) * S) == cudaSuccess &&
-            cudaMallocHost(&E->h_out, static_cast<size_t>(kOutStride) * S) == cudaSuccess &&
-            cudaMallocHost(&E->h_valid, sizeof(uint32_t) * S) == cudaSuccess;
+            cudaMalloc(&E->d_cursors, sizeof(unsigned int) * (kVariants + 1)) == cudaSuccess;
+  {
+    HostStage& h = E->stage;
+    ok = ok && cudaMallocHost(&h.queries, sizeof(QueryDesc) * S) == cudaSuccess &&
+         cudaMallocHost(&h.jobs_left, sizeof(unsigned int) * S) == cudaSuccess &&
+         cudaMallocHost(&h.out, static_cast<size_t>(kOutStride) * S) == cudaSuccess &&
+         cudaMallocHost(&h.valid, sizeof(uint32_t) * S) == cudaSuccess &&
+         cudaEventCreate(&h.start) == cudaSuccess && cudaEventCreate(&h.done) == cudaSuccess;
+    if (ok) {
+      std::memset(h.queries, 0, sizeof(QueryDesc) * S);
+      std::memset(h.jobs_left, 0, sizeof(unsigned int) * S);
+    }
+  }
   return ok;
 }
 
@@ -312,21 +328,27 @@ void free_engine(ServeEngine* E) {
   cudaFree(E->d_job_ctr);
   cudaFree(E->d_tails);
   cudaFree(E->d_tail_query);
-  cudaFreeHost(E->h_jobs);
-  cudaFreeHost(E->h_job_query);
-  cudaFreeHost(E->h_job_tiles);
-  cudaFreeHost(E->h_tails);
-  cudaFreeHost(E->h_tail_query);
-  cudaFreeHost(E->h_queries);
-  cudaFreeHost(E->h_jobs_left);
-  cudaFreeHost(E->h_out);
-  cudaFreeHost(E->h_valid);
+  {
+    HostStage& h = E->stage;
+    cudaFreeHost(h.jobs);
+    cudaFreeHost(h.job_query);
+    cudaFreeHost(h.job_tiles);
+    cudaFreeHost(h.tails);
+    cudaFreeHost(h.tail_query);
+    cudaFreeHost(h.queries);
+    cudaFreeHost(h.jobs_left);
+    cudaFreeHost(h.out);
+    cudaFreeHost(h.valid);
+    if (h.start) cudaEventDestroy(h.start);
+    if (h.done) cudaEventDestroy(h.done);
+  }
   if (E->stream) cudaStreamDestroy(E->stream);
 }
 
-// One iteration over the active queries.  Returns false on a CUDA error (every
-// in-flight query is then failed with BBP_ECUDA).
-bool run_iteration(ServeEngine* E, std::vector<Query*>& batch, std::vector<int>& fresh_slots) {
+// Plans one iteration over the active queries into staging H and enqueues it
+// (uploads, launches, result download, events).  Queries whose
+// last piece is in it move to H.finishing.  Returns false on a CUDA error.
+bool enqueue_iteration(ServeEngine* E, HostStage& H, std::vector<Query*>& batch, std::vector<int>& fresh_slots) {
   bbp_plan p = E->plan;
   const uint64_t tile = 32ull * p->streams * p->run;
   const uint64_t budget_terms = static_cast<uint64_t>(E->rate * kIterTargetSeconds);
@@ -335,13 +357,16 @@ bool run_iteration(ServeEngine* E, std::vector<Query*>& batch, std::vector<int>&
   std::vector<Piece> pieces;
   uint64_t terms = 0;
   std::vector<uint32_t> npieces(batch.size(), 0);
+  H.finishing.clear();
   for (size_t i = 0; i < batch.size(); ++i) {
     Query* q = batch[i];
     const size_t before = pieces.size();
     take_pieces(E, q, share, pieces, &terms);
     npieces[i] = static_cast<uint32_t>(pieces.size() - before);
     q->final_in_flight = q->next >= q->work.size();
+    if (q->final_in_flight) H.finishing.push_back(q);
   }
+  H.terms = terms;
   // group head pieces by variant, tails apart
   std::vector<uint32_t> vb(kVariants + 1, 0);
   std::vector<const Piece*> heads, tails;
@@ -354,45 +379,46 @@ bool run_iteration(ServeEngine* E, std::vector<Query*>& batch, std::vector<int>&
   for (const Piece& pc : pieces)
     if (pc.tail) tails.push_back(&pc);
   const size_t nh = heads.size(), nt = tails.size();
-  if (!grow_pinned(&E->h_jobs, &E->hc_jobs, nh) || !grow_pinned(&E->h_job_query, &E->hc_job_query, nh) ||
-      !grow_pinned(&E->h_job_tiles, &E->hc_job_tiles, nh) || !grow_pinned(&E->h_tails, &E->hc_tails, nt) ||
-      !grow_pinned(&E->h_tail_query, &E->hc_tail_query, nt) || !grow_dev(&E->d_jobs, &E->c_jobs, nh) ||
+  if (!grow_pinned(&H.jobs, &H.c_jobs, nh) || !grow_pinned(&H.job_query, &H.c_job_query, nh) ||
+      !grow_pinned(&H.job_tiles, &H.c_job_tiles, nh) || !grow_pinned(&H.tails, &H.c_tails, nt) ||
+      !grow_pinned(&H.tail_query, &H.c_tail_query, nt) || !grow_dev(&E->d_jobs, &E->c_jobs, nh) ||
       !grow_dev(&E->d_job_query, &E->c_job_query, nh) || !grow_dev(&E->d_job_tiles, &E->c_job_tiles, nh) ||
       !grow_dev(&E->d_job_ctr, &E->c_job_ctr, 2 * nh) || !grow_dev(&E->d_tails, &E->c_tails, nt) ||
       !grow_dev(&E->d_tail_query, &E->c_tail_query, nt))
     return false;
   for (size_t i = 0; i < nh; ++i) {
-    E->h_jobs[i] = heads[i]->head;
-    E->h_job_query[i] = heads[i]->slot;
-    E->h_job_tiles[i] = heads[i]->tiles;
+    H.jobs[i] = heads[i]->head;
+    H.job_query[i] = heads[i]->slot;
+    H.job_tiles[i] = heads[i]->tiles;
   }
   for (size_t i = 0; i < nt; ++i) {
-    E->h_tails[i] = tails[i]->tailargs;
-    E->h_tail_query[i] = tails[i]->slot;
+    H.tails[i] = tails[i]->tailargs;
+    H.tail_query[i] = tails[i]->slot;
   }
-  cudaStream_t s = E->stream;
-  cudaError_t e = cudaSuccess;
-  auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
-  for (int slot : fresh_slots)
-    chk(cudaMemsetAsync(E->d_accum + static_cast<uint64_t>(slot) * kMaxLimbs, 0,
-                        sizeof(unsigned long long) * kMaxLimbs, s));
   for (size_t i = 0; i < batch.size(); ++i) {
     Query* q = batch[i];
-    QueryDesc& Q = E->h_queries[q->slot];
+    QueryDesc& Q = H.queries[q->slot];
     Q.bound = q->bound;
     Q.P = q->P;
     Q.L = q->L;
     Q.out_offset = static_cast<uint32_t>(q->slot) * kOutStride;
-    E->h_jobs_left[q->slot] = npieces[i] + (q->final_in_flight ? 0u : 1u);  // hold while work remains
-    chk(cudaMemcpyAsync(E->d_queries + q->slot, &Q, sizeof(QueryDesc), cudaMemcpyHostToDevice, s));
-    chk(cudaMemcpyAsync(E->d_jobs_left + q->slot, &E->h_jobs_left[q->slot], sizeof(unsigned int),
-                        cudaMemcpyHostToDevice, s));
+    H.jobs_left[q->slot] = npieces[i] + (q->final_in_flight ? 0u : 1u);  // hold while work remains
   }
-  chk(cudaMemcpyAsync(E->d_jobs, E->h_jobs, sizeof(HeadArgs) * nh, cudaMemcpyHostToDevice, s));
-  chk(cudaMemcpyAsync(E->d_job_query, E->h_job_query, sizeof(uint32_t) * nh, cudaMemcpyHostToDevice, s));
-  chk(cudaMemcpyAsync(E->d_job_tiles, E->h_job_tiles, sizeof(uint64_t) * nh, cudaMemcpyHostToDevice, s));
-  chk(cudaMemcpyAsync(E->d_tails, E->h_tails, sizeof(TailArgs) * nt, cudaMemcpyHostToDevice, s));
-  chk(cudaMemcpyAsync(E->d_tail_query, E->h_tail_query, sizeof(uint32_t) * nt, cudaMemcpyHostToDevice, s));
+  cudaStream_t s = E->stream;
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+  chk(cudaEventRecord(H.start, s));
+  for (int slot : fresh_slots)
+    chk(cudaMemsetAsync(E->d_accum + static_cast<uint64_t>(slot) * kMaxLimbs, 0,
+                        sizeof(unsigned long long) * kMaxLimbs, s));
+  // the whole slot tables in two copies (slots not in this iteration have no jobs)
+  chk(cudaMemcpyAsync(E->d_queries, H.queries, sizeof(QueryDesc) * E->max_slots, cudaMemcpyHostToDevice, s));
+  chk(cudaMemcpyAsync(E->d_jobs_left, H.jobs_left, sizeof(unsigned int) * E->max_slots, cudaMemcpyHostToDevice, s));
+  chk(cudaMemcpyAsync(E->d_jobs, H.jobs, sizeof(HeadArgs) * nh, cudaMemcpyHostToDevice, s));
+  chk(cudaMemcpyAsync(E->d_job_query, H.job_query, sizeof(uint32_t) * nh, cudaMemcpyHostToDevice, s));
+  chk(cudaMemcpyAsync(E->d_job_tiles, H.job_tiles, sizeof(uint64_t) * nh, cudaMemcpyHostToDevice, s));
+  chk(cudaMemcpyAsync(E->d_tails, H.tails, sizeof(TailArgs) * nt, cudaMemcpyHostToDevice, s));
+  chk(cudaMemcpyAsync(E->d_tail_query, H.tail_query, sizeof(uint32_t) * nt, cudaMemcpyHostToDevice, s));
   chk(cudaMemsetAsync(E->d_job_ctr, 0, sizeof(unsigned long long) * 2 * std::max<size_t>(nh, 1), s));
   chk(cudaMemsetAsync(E->d_cursors, 0, sizeof(unsigned int) * (kVariants + 1), s));
   BatchDev dev{};
@@ -403,14 +429,13 @@ bool run_iteration(ServeEngine* E, std::vector<Query*>& batch, std::vector<int>&
   dev.job_done = E->d_job_ctr + nh;
   dev.tails = E->d_tails;
   dev.tail_query = E->d_tail_query;
-  dev.grab = static_cast<uint32_t>(p->grab);
+  dev.grab = 1;  // short iterations: hand out single tiles so every launch ends evenly
   dev.queries = E->d_queries;
   dev.accum = E->d_accum;
   dev.jobs_left = E->d_jobs_left;
   dev.out = E->d_out;
   dev.valid = E->d_valid;
   dev.done_ns = E->d_done;
-  const double t0 = now_s();
   chk(launch_queue_tail(dev, 0, static_cast<uint32_t>(nt), E->d_cursors + kVariants, p->sm_count * 4, s));
   for (int v = 0; v < kVariants; ++v) {
     if (vb[v] == vb[v + 1]) continue;
@@ -418,20 +443,54 @@ bool run_iteration(ServeEngine* E, std::vector<Query*>& batch, std::vector<int>&
     const int blocks = queue_occupancy(path, p->streams, lmax) * p->sm_count;
     chk(launch_queue(dev, vb[v], vb[v + 1], E->d_cursors + v, path, p->streams, lmax, blocks, s));
   }
-  // results of the queries that finished in this iteration
-  for (Query* q : batch) {
-    if (!q->final_in_flight) continue;
-    chk(cudaMemcpyAsync(E->h_out + static_cast<size_t>(q->slot) * kOutStride,
-                        E->d_out + static_cast<size_t>(q->slot) * kOutStride, (q->P + 7) / 8, cudaMemcpyDeviceToHost, s));
-    chk(cudaMemcpyAsync(E->h_valid + q->slot, E->d_valid + q->slot, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  if (!H.finishing.empty()) {  // results of the queries that finish in this iteration
+    chk(cudaMemcpyAsync(H.out, E->d_out, static_cast<size_t>(kOutStride) * E->max_slots, cudaMemcpyDeviceToHost, s));
+    chk(cudaMemcpyAsync(H.valid, E->d_valid, sizeof(uint32_t) * E->max_slots, cudaMemcpyDeviceToHost, s));
   }
-  chk(cudaStreamSynchronize(s));
-  const double dt = now_s() - t0;
-  if (e != cudaSuccess) return false;
-  if (dt > 1e-4 && terms > 0) E->rate = 0.7 * E->rate + 0.3 * (static_cast<double>(terms) / dt);
+  chk(cudaEventRecord(H.done, s));
+  H.in_flight = e == cudaSuccess;
+  return e == cudaSuccess;
+}
+
+// Waits for an enqueued iteration and publishes the queries it finished (under
+// E->mu, which bbp_poll and bbp_serve_stats take too).
+bool finish_iteration(ServeEngine* E, HostStage& H) {
+  if (!H.in_flight) return true;
+  H.in_flight = false;
+  if (cudaEventSynchronize(H.done) != cudaSuccess) return false;
+  float ms = 0;
+  const bool timed = cudaEventElapsedTime(&ms, H.start, H.done) == cudaSuccess && ms > 0.1f && H.terms > 0;
+  std::lock_guard<std::mutex> lock(E->mu);
+  if (timed) E->rate = 0.7 * E->rate + 0.3 * (static_cast<double>(H.terms) / (1e-3 * ms));
   E->iterations++;
-  E->terms_done += terms;
+  E->terms_done += H.terms;
+  for (Query* q : H.finishing) {
+    q->out.assign(H.out + static_cast<size_t>(q->slot) * kOutStride,
+                  H.out + static_cast<size_t>(q->slot) * kOutStride + (q->P + 7) / 8);
+    q->valid = H.valid[q->slot];
+    q->state = kDone;
+    E->free_slots.push_back(q->slot);
+    q->slot = -1;
+    q->work.clear();
+    q->work.shrink_to_fit();
+  }
+  H.finishing.clear();
   return true;
+}
+
+void fail_all(ServeEngine* E) {
+  std::lock_guard<std::mutex> lock(E->mu);
+  for (Query* q : E->stage.finishing) {
+    q->state = kFailed;
+    q->error = BBP_ECUDA;
+  }
+  E->stage.finishing.clear();
+  E->stage.in_flight = false;
+  for (Query* q : E->active) {
+    q->state = kFailed;
+    q->error = BBP_ECUDA;
+  }
+  E->active.clear();
 }
 
 void engine_main(ServeEngine* E) {
@@ -454,28 +513,16 @@ void engine_main(ServeEngine* E) {
       }
       batch = E->active;
     }
-    const bool ok = run_iteration(E, batch, fresh);
-    std::lock_guard<std::mutex> lock(E->mu);
-    std::vector<Query*> still;
-    for (Query* q : E->active) {
-      if (!ok) {
-        q->state = kFailed;
-        q->error = BBP_ECUDA;
-      } else if (q->final_in_flight) {
-        q->out.assign(E->h_out + static_cast<size_t>(q->slot) * kOutStride,
-                      E->h_out + static_cast<size_t>(q->slot) * kOutStride + (q->P + 7) / 8);
-        q->valid = E->h_valid[q->slot];
-        q->state = kDone;
-      } else {
-        still.push_back(q);
-        continue;
-      }
-      E->free_slots.push_back(q->slot);
-      q->slot = -1;
-      q->work.clear();
-      q->work.shrink_to_fit();
+    bool ok = enqueue_iteration(E, E->stage, batch, fresh);
+    {
+      std::lock_guard<std::mutex> lock(E->mu);  // queries handed out completely leave the active list
+      std::vector<Query*> still;
+      for (Query* q : E->active)
+        if (!q->final_in_flight) still.push_back(q);
+      E->active.swap(still);
     }
-    E->active.swap(still);
+    ok = ok && finish_iteration(E, E->stage);
+    if (!ok) fail_all(E);
   }
 }
 
@@ -517,6 +564,7 @@ void release_serve_state(bbp_plan p) {
   }
   E->cv.notify_all();
   if (E->thread.joinable()) E->thread.join();
+  if (E->stream) cudaStreamSynchronize(E->stream);
   for (auto& kv : E->tickets) delete kv.second;
   free_engine(E);
   delete E;
