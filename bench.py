@@ -212,9 +212,9 @@ def expected_bits_check(bits_value: int, valid: int) -> bool:
     return valid == P_BITS and (bits_value & ((1 << 255) - 1)) == ref >> (row["bits"] - 255)
 
 
-def head_kernel_traffic():
-    """DRAM bytes per head-kernel launch from the committed ncu capture, if the
-    kernel sources are still the ones that capture measured (else None)."""
+def head_kernel_ncu():
+    """The committed ncu record of the head kernel (DRAM bytes per launch, FMA-pipe
+    use), if the kernel sources are still the ones that capture measured (else {})."""
     import hashlib
 
     path = os.path.join(ROOT, "profiles", "head_kernel_traffic.json")
@@ -226,10 +226,10 @@ def head_kernel_traffic():
             with open(os.path.join(ROOT, f), "rb") as src:
                 h.update(src.read())
         if h.hexdigest() == rec["kernel_sources_sha256"]:
-            return rec["dram_bytes_per_launch"]
+            return rec
     except (OSError, KeyError, ValueError):
         pass
-    return None
+    return {}
 
 
 def run_gpu(args):
@@ -343,6 +343,7 @@ def run_gpu(args):
     achieved = (imad / (head_ms / 1e3)) / 1e12 if head_ms > 0 else None
     value = terms / t_dev
     e2e_value = terms / t_e2e
+    ncu = head_kernel_ncu()
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -361,7 +362,8 @@ def run_gpu(args):
                 "note": "bbp_bits with host output; the query (n, P) travels as kernel arguments"},
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T IMAD/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": head_kernel_traffic(),
+                     "frac": (achieved / peak) if achieved else None, "traffic": ncu.get("dram_bytes_per_launch"),
+                     "ncu_imad_pipe_frac": ncu.get("fma_pipe_frac_of_imad_rate"),
                      "kernel": "head_kernel", "head_launches": head_launches,
                      "peak_basis": f"{sms} SMs x {IMAD_LANES_PER_CLK_PER_SM} IMAD lanes/clk x {max_mhz:.0f} MHz"},
         "cpu_baseline": cpu,
