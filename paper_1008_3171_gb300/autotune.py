@@ -3,13 +3,19 @@
 Sweeps the launch parameters the C ABI reads from a tune table
 (bbp_plan_opts.tune_table) and writes the fastest setting as JSON:
 
-* run     -- consecutive terms per stream (R mod m is carried along a run),
-* streams -- independent pairs of terms per thread (instruction-level parallelism),
-* grab    -- warp tiles handed out per queue operation in batched passes.
+* run           -- consecutive terms per stream (R mod m is carried along a run),
+* streams       -- independent pairs of terms per thread (instruction-level parallelism),
+* cta           -- threads per CTA of the single-query head kernel,
+* limb_bump     -- accumulator limb class above the smallest that holds W bits,
+* wide_min_bits -- Montgomery width: moduli of at least this many bits use the
+                   two-limb (64-bit) path, smaller ones the one-limb (32-bit) path,
+* grab          -- warp tiles handed out per queue operation in batched passes.
 
-run x streams are timed on a slice of the n = 1e12 query (series 0, 1e9 terms of
-the 64-bit path); grab on a seeded calibration batch.  Every setting computes
-bit-identical results (the sum is exact), so only time is compared.
+run x streams, then cta, then limb_bump are timed on a slice of the n = 1e12
+query (series 0, 1e9 terms of the 64-bit path); wide_min_bits on the whole
+n = 1e9, P = 128 query (moduli up to 2^30); grab on a seeded calibration batch.
+Every setting computes bit-identical results (the sum is exact; the sweep checks
+it), so only time is compared.
 
     python -m paper_1008_3171_gb300.autotune --out tune.json
 """
@@ -28,13 +34,16 @@ sys.path.insert(0, os.path.dirname(_HERE))
 
 RUNS = (16, 32, 64, 128)
 STREAMS = (1, 2)
+CTAS = (64, 128, 256)
+LIMB_BUMPS = (0, 1)
+WIDE_MIN_BITS = (16, 22, 26, 30)
 GRABS = (2, 4, 8, 16, 32)
 
 
-def _plan(bbp, run, streams, grab):
+def _plan(bbp, **setting):
     fd, path = tempfile.mkstemp(suffix=".json")
     with os.fdopen(fd, "w") as fh:
-        json.dump({"run": run, "streams": streams, "grab": grab}, fh)
+        json.dump(setting, fh)
     try:
         return bbp.Plan(device=0, guard_bits=64, tune_table=path)
     finally:
@@ -52,59 +61,84 @@ def _time(fn, reps=3):
     return best
 
 
+def _sweep(bbp, name, values, base, work, measured, reps=3):
+    """Times work(plan) for each value of `name` on top of `base`; every value must
+    give the result of the first.  Returns the fastest value."""
+    ref = None
+    best = None
+    measured[name] = {}
+    for v in values:
+        p = _plan(bbp, **{**base, name: v})
+        try:
+            holder = {}
+
+            def one():
+                holder["r"] = work(p)
+
+            dt = _time(one, reps)
+            if ref is None:
+                ref = holder["r"][0]
+            if holder["r"][0] != ref:
+                raise RuntimeError(f"{name}={v} changed the result")
+            measured[name][str(v)] = holder["r"][1] / dt
+            if best is None or dt < best[0]:
+                best = (dt, v)
+        finally:
+            p.close()
+    return best[1]
+
+
 def tune(out_path: str, slice_terms: int = 1_000_000_000, batch: int = 512) -> dict:
     import paper_1008_3171_gb300 as bbp
     import workloads
 
-    measured = {"single": {}, "batch": {}}
-    ref = None
-    best = None
+    measured = {}
     kb = 50_000_000_000
+
+    def slice_work(p):
+        return p.partial_sum(0, 0, kb, kb + slice_terms, 10**12, 256), slice_terms
+
+    # run x streams jointly (they trade registers against each other)
+    measured["run,streams"] = {}
+    ref, best = None, None
     for run in RUNS:
         for streams in STREAMS:
-            p = _plan(bbp, run, streams, 8)
+            p = _plan(bbp, run=run, streams=streams)
             try:
                 holder = {}
 
                 def one():
-                    holder["v"] = p.partial_sum(0, 0, kb, kb + slice_terms, 10**12, 256)
+                    holder["v"] = slice_work(p)[0]
 
                 dt = _time(one)
                 if ref is None:
                     ref = holder["v"]
                 if holder["v"] != ref:
                     raise RuntimeError(f"run={run} streams={streams} changed the sum")
-                measured["single"][f"run={run},streams={streams}"] = slice_terms / dt
+                measured["run,streams"][f"{run},{streams}"] = slice_terms / dt
                 if best is None or dt < best[0]:
                     best = (dt, run, streams)
             finally:
                 p.close()
-    _, run, streams = best
+    setting = {"run": best[1], "streams": best[2]}
+    setting["cta"] = _sweep(bbp, "cta", CTAS, setting, slice_work, measured)
+    setting["limb_bump"] = _sweep(bbp, "limb_bump", LIMB_BUMPS, setting, slice_work, measured)
+
+    def n1e9_work(p):
+        v = p.bits(10**9, 128)
+        return v, p.stats()["terms"]
+
+    setting["wide_min_bits"] = _sweep(bbp, "wide_min_bits", WIDE_MIN_BITS, setting, n1e9_work, measured, reps=5)
     ns, Ps = workloads.batched_queries(count=batch, seed=3, lo=4.0, hi=8.5)
-    ref = None
-    best_g = None
-    for grab in GRABS:
-        p = _plan(bbp, run, streams, grab)
-        try:
-            holder = {}
 
-            def one():
-                holder["v"] = bbp.bbp_bits_batch(p.handle, 0, ns, Ps, with_latency=False)[:2]
+    def batch_work(p):
+        r = bbp.bbp_bits_batch(p.handle, 0, ns, Ps, with_latency=False)[:2]
+        return r, p.stats()["terms"]
 
-            dt = _time(one, reps=2)
-            if ref is None:
-                ref = holder["v"]
-            if holder["v"] != ref:
-                raise RuntimeError(f"grab={grab} changed the results")
-            measured["batch"][f"grab={grab}"] = p.stats()["terms"] / dt
-            if best_g is None or dt < best_g[0]:
-                best_g = (dt, grab)
-        finally:
-            p.close()
+    setting["grab"] = _sweep(bbp, "grab", GRABS, setting, batch_work, measured, reps=2)
     import torch
 
-    table = {"run": run, "streams": streams, "grab": best_g[1],
-             "device": torch.cuda.get_device_name(0), "measured_terms_per_s": measured}
+    table = {**setting, "device": torch.cuda.get_device_name(0), "measured_terms_per_s": measured}
     with open(out_path, "w") as fh:
         json.dump(table, fh, indent=1)
         fh.write("\n")

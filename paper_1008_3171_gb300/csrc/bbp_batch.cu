@@ -170,7 +170,7 @@ static bbp_status plan_batch(bbp_plan p, int f, uint32_t count, const uint64_t* 
     ranges.clear();
     uint64_t N = 0;
     for (uint32_t j = 0; j < F.count; ++j) {
-      const int st = plan_series(F, j, n[q], W, static_cast<uint32_t>(lmax), 0, UINT64_MAX, ranges);
+      const int st = plan_series(F, j, n[q], W, static_cast<uint32_t>(lmax), 0, UINT64_MAX, ranges, p->wide_min_bits);
       if (st == -6) return BBP_ERANGE;
       if (st != 0) return BBP_EINVAL;
       N += natural_end(F, j, n[q] - 1, W);

@@ -9,6 +9,8 @@
 //   imad_probe     -- issue-rate microbenchmark of the integer multiply pipe.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "bbp_device.cuh"
 #include "bbp_kernels.cuh"
 
@@ -539,54 +541,58 @@ namespace {
 constexpr int kLmaxList[] = {3, 4, 6, 10, 16, 40};
 
 template <int LMAX, int PATH, int S>
-cudaError_t launch_head_t(const HeadArgs& a, int blocks, cudaStream_t s) {
+cudaError_t launch_head_t(const HeadArgs& a, int blocks, int threads, cudaStream_t s) {
   const uint64_t tile = 32ull * S * a.run;
   const uint64_t ntiles = (a.count + tile - 1) / tile;
-  head_kernel<LMAX, PATH, S><<<blocks, kHeadThreads, 0, s>>>(a, ntiles);
+  head_kernel<LMAX, PATH, S><<<blocks, threads, 0, s>>>(a, ntiles);
   return cudaGetLastError();
 }
 
 template <int LMAX, int PATH, int S>
-int occupancy_t() {
+int occupancy_t(int threads) {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, head_kernel<LMAX, PATH, S>, kHeadThreads, 0) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, head_kernel<LMAX, PATH, S>, threads, 0) != cudaSuccess)
     return 1;
   return n > 0 ? n : 1;
 }
 
 template <int LMAX, int PATH>
-int occupancy_p(int streams) {
-  return streams == 2 ? occupancy_t<LMAX, PATH, 2>() : occupancy_t<LMAX, PATH, 1>();
+int occupancy_p(int streams, int threads) {
+  return streams == 2 ? occupancy_t<LMAX, PATH, 2>(threads) : occupancy_t<LMAX, PATH, 1>(threads);
 }
 
 template <int LMAX>
-int occupancy_l(int path, int streams) {
-  if (path == 2) return occupancy_p<LMAX, 2>(streams);
-  if (path == 1) return occupancy_p<LMAX, 1>(streams);
-  return occupancy_p<LMAX, 0>(streams);
+int occupancy_l(int path, int streams, int threads) {
+  if (path == 2) return occupancy_p<LMAX, 2>(streams, threads);
+  if (path == 1) return occupancy_p<LMAX, 1>(streams, threads);
+  return occupancy_p<LMAX, 0>(streams, threads);
 }
 
 template <int LMAX, int PATH>
-cudaError_t launch_head_p(const HeadArgs& a, int streams, int blocks, cudaStream_t s) {
-  return streams == 2 ? launch_head_t<LMAX, PATH, 2>(a, blocks, s) : launch_head_t<LMAX, PATH, 1>(a, blocks, s);
+cudaError_t launch_head_p(const HeadArgs& a, int streams, int blocks, int threads, cudaStream_t s) {
+  return streams == 2 ? launch_head_t<LMAX, PATH, 2>(a, blocks, threads, s)
+                      : launch_head_t<LMAX, PATH, 1>(a, blocks, threads, s);
 }
 
 template <int LMAX>
-cudaError_t launch_head_l(const HeadArgs& a, int path, int streams, int blocks, cudaStream_t s) {
-  if (path == 2) return launch_head_p<LMAX, 2>(a, streams, blocks, s);
-  if (path == 1) return launch_head_p<LMAX, 1>(a, streams, blocks, s);
-  return launch_head_p<LMAX, 0>(a, streams, blocks, s);
+cudaError_t launch_head_l(const HeadArgs& a, int path, int streams, int blocks, int threads, cudaStream_t s) {
+  if (path == 2) return launch_head_p<LMAX, 2>(a, streams, blocks, threads, s);
+  if (path == 1) return launch_head_p<LMAX, 1>(a, streams, blocks, threads, s);
+  return launch_head_p<LMAX, 0>(a, streams, blocks, threads, s);
 }
+
+bool valid_head_threads(int threads) { return threads >= 32 && threads <= kHeadThreads && threads % 32 == 0; }
 }  // namespace
 
-int head_occupancy(int path, int streams, int lmax) {
+int head_occupancy(int path, int streams, int lmax, int threads) {
+  if (!valid_head_threads(threads)) return 1;
   switch (lmax) {
-    case 3: return occupancy_l<3>(path, streams);
-    case 4: return occupancy_l<4>(path, streams);
-    case 6: return occupancy_l<6>(path, streams);
-    case 10: return occupancy_l<10>(path, streams);
-    case 16: return occupancy_l<16>(path, streams);
-    case 40: return occupancy_l<40>(path, streams);
+    case 3: return occupancy_l<3>(path, streams, threads);
+    case 4: return occupancy_l<4>(path, streams, threads);
+    case 6: return occupancy_l<6>(path, streams, threads);
+    case 10: return occupancy_l<10>(path, streams, threads);
+    case 16: return occupancy_l<16>(path, streams, threads);
+    case 40: return occupancy_l<40>(path, streams, threads);
     default: return 1;
   }
 }
@@ -666,20 +672,22 @@ cudaError_t launch_queue_tail(const BatchDev& b, uint32_t tail_begin, uint32_t t
   return cudaGetLastError();
 }
 
-int head_lmax_for(int L) {
-  for (int v : kLmaxList)
-    if (v >= L) return v;
+int head_lmax_for(int L, int bump) {
+  constexpr int n = static_cast<int>(sizeof(kLmaxList) / sizeof(kLmaxList[0]));
+  for (int i = 0; i < n; ++i)
+    if (kLmaxList[i] >= L) return kLmaxList[std::min(n - 1, i + std::max(0, bump))];
   return 0;
 }
 
-cudaError_t launch_head(const HeadArgs& a, int path, int streams, int lmax, int blocks, cudaStream_t s) {
+cudaError_t launch_head(const HeadArgs& a, int path, int streams, int lmax, int blocks, cudaStream_t s, int threads) {
+  if (!valid_head_threads(threads)) return cudaErrorInvalidValue;
   switch (lmax) {
-    case 3: return launch_head_l<3>(a, path, streams, blocks, s);
-    case 4: return launch_head_l<4>(a, path, streams, blocks, s);
-    case 6: return launch_head_l<6>(a, path, streams, blocks, s);
-    case 10: return launch_head_l<10>(a, path, streams, blocks, s);
-    case 16: return launch_head_l<16>(a, path, streams, blocks, s);
-    case 40: return launch_head_l<40>(a, path, streams, blocks, s);
+    case 3: return launch_head_l<3>(a, path, streams, blocks, threads, s);
+    case 4: return launch_head_l<4>(a, path, streams, blocks, threads, s);
+    case 6: return launch_head_l<6>(a, path, streams, blocks, threads, s);
+    case 10: return launch_head_l<10>(a, path, streams, blocks, threads, s);
+    case 16: return launch_head_l<16>(a, path, streams, blocks, threads, s);
+    case 40: return launch_head_l<40>(a, path, streams, blocks, threads, s);
     default: return cudaErrorInvalidValue;
   }
 }

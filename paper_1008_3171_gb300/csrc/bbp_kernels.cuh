@@ -78,7 +78,9 @@ struct BatchDev {
 // Launch helpers (defined in bbp_kernels.cu).  They return cudaGetLastError().
 // path: 0 = 32-bit moduli (bitlen <= 29), 1 = 64-bit moduli with bitlen <= 47,
 //       2 = 64-bit moduli with bitlen <= 60.
-cudaError_t launch_head(const HeadArgs& a, int path, int streams, int lmax, int blocks, cudaStream_t s);
+// threads: CTA size, a multiple of 32 in [32, kHeadThreads] (else cudaErrorInvalidValue).
+cudaError_t launch_head(const HeadArgs& a, int path, int streams, int lmax, int blocks, cudaStream_t s,
+                        int threads = kHeadThreads);
 cudaError_t launch_tail(const TailArgs& a, cudaStream_t s);
 cudaError_t launch_zero_slots(unsigned long long* slots, int L, cudaStream_t s);
 cudaError_t launch_fold_limbs(const unsigned long long* slots, int L, uint32_t* out_limbs, cudaStream_t s);
@@ -93,8 +95,11 @@ cudaError_t launch_queue_tail(const BatchDev& b, uint32_t tail_begin, uint32_t t
                               int blocks, cudaStream_t s);
 cudaError_t launch_timestamp(unsigned long long* where, cudaStream_t s);
 int queue_occupancy(int path, int streams, int lmax);
-int head_lmax_for(int L);  // smallest compiled limb capacity >= L, or 0
-int head_occupancy(int path, int streams, int lmax);  // resident CTAs per SM of that instantiation
+// Smallest compiled limb capacity >= L (bump > 0: that many classes larger, capped at
+// the largest), or 0 when L exceeds every class.
+int head_lmax_for(int L, int bump = 0);
+// Resident CTAs per SM of that instantiation at `threads` per CTA.
+int head_occupancy(int path, int streams, int lmax, int threads = kHeadThreads);
 cudaError_t launch_imad_probe(int kind, int blocks, int threads, int iters, unsigned long long* cycles_out,
                               uint32_t* smid_out, uint32_t* sink, cudaStream_t s);
 

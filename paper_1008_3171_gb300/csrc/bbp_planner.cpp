@@ -81,7 +81,9 @@ void window_params(int path, int lbits, uint8_t* window, uint8_t* first) {
   *first = static_cast<uint8_t>(h);
 }
 
-int path_for_bits(int lbits) { return lbits < kWideMinBits ? 0 : (lbits <= kSmallMaxBits ? 1 : 2); }
+int path_for_bits(int lbits, int wide_min_bits) {
+  return lbits < std::min(wide_min_bits, kWideMinBits) ? 0 : (lbits <= kSmallMaxBits ? 1 : 2);
+}
 
 double head_term_imad(int path, int nb, int first, int lmax) {
   const int h = nb > 0 ? std::min(first, nb - 1) : 0;
@@ -123,8 +125,9 @@ double range_imad(const FormulaDef& f, const SeriesDef& s, uint64_t d, uint32_t 
 }  // namespace
 
 int plan_series(const FormulaDef& f, uint32_t j, uint64_t n, uint32_t W, uint32_t lmax, uint64_t k_lo,
-                uint64_t k_hi, std::vector<TermRange>& out) {
+                uint64_t k_hi, std::vector<TermRange>& out, int wide_min_bits) {
   if (n == 0 || j >= f.count || W == 0 || W % 32 != 0 || W > kMaxWorkingBits) return -1;
+  if (wide_min_bits < 2 || wide_min_bits > kWideMinBits) return -1;
   const SeriesDef& s = f.s[j];
   const uint64_t d = n - 1;
   const uint64_t he = head_end(f, j, d);
@@ -145,7 +148,7 @@ int plan_series(const FormulaDef& f, uint32_t j, uint64_t n, uint32_t W, uint32_
       uint64_t k0 = std::max(head_lo, first_k_at_least(1ull << (l - 1), s.a, s.b));
       uint64_t k1 = std::min(head_hi, first_k_at_least(1ull << l, s.a, s.b));
       if (k0 >= k1) continue;
-      const int path = path_for_bits(l);
+      const int path = path_for_bits(l, wide_min_bits);
       uint8_t w, h;
       window_params(path, l, &w, &h);
       if (!groups.empty() && groups.back().path == path && groups.back().w == w && groups.back().h == h &&

@@ -49,8 +49,10 @@ bool working_bits(uint32_t P, uint32_t G, uint32_t* W);
 uint64_t head_end(const FormulaDef& f, uint32_t j, uint64_t d);
 uint64_t natural_end(const FormulaDef& f, uint32_t j, uint64_t d, uint32_t W);
 
-// Kernel path for moduli of `lbits` bits.
-int path_for_bits(int lbits);
+// Kernel path for moduli of `lbits` bits: 0 (32-bit Montgomery) below
+// `wide_min_bits`, else 1 or 2 (64-bit).  wide_min_bits may be lowered from
+// kWideMinBits (a tuning choice: small moduli on the 64-bit path) but not raised.
+int path_for_bits(int lbits, int wide_min_bits = kWideMinBits);
 
 // Ladder parameters for moduli of at most `lbits` bits on the given path.
 void window_params(int path, int lbits, uint8_t* window, uint8_t* first);
@@ -70,8 +72,9 @@ void shard_range(const FormulaDef& f, uint32_t j, uint64_t n, uint32_t W, uint32
                  uint64_t* k_begin, uint64_t* k_end);
 
 // Appends the ranges of series j restricted to k in [k_lo, k_hi) (k_hi = UINT64_MAX:
-// natural end).  Returns 0, or -6 (modulus too large) / -1 (bad argument).
+// natural end).  Returns 0, or -6 (modulus too large) / -1 (bad argument, including
+// wide_min_bits outside [2, kWideMinBits]).
 int plan_series(const FormulaDef& f, uint32_t j, uint64_t n, uint32_t W, uint32_t lmax, uint64_t k_lo,
-                uint64_t k_hi, std::vector<TermRange>& out);
+                uint64_t k_hi, std::vector<TermRange>& out, int wide_min_bits = kWideMinBits);
 
 }  // namespace bbp

@@ -41,7 +41,7 @@ constexpr int kDefaultRun = 64;
 
 bool valid_formula(int f) { return f == BBP_BELLARD || f == BBP_BBP; }
 
-int pick_lmax(uint32_t W) { return head_lmax_for(static_cast<int>(W / 32)); }
+int pick_lmax(uint32_t W, int bump) { return head_lmax_for(static_cast<int>(W / 32), bump); }
 
 }  // namespace
 
@@ -174,7 +174,7 @@ bbp_status launch_ranges(bbp_plan p, int f, uint64_t n, uint32_t W, const std::v
                          unsigned long long* slots, cudaStream_t st) {
   const FormulaDef& F = formula_def(f);
   const uint32_t L = W / 32;
-  const int lmax = pick_lmax(W);
+  const int lmax = pick_lmax(W, p->limb_bump);
   if (lmax == 0) return BBP_EINVAL;
   float total_ms = 0;
   for (const TermRange& r : ranges) {
@@ -218,12 +218,12 @@ bbp_status launch_ranges(bbp_plan p, int f, uint64_t n, uint32_t W, const std::v
     const int streams = p->streams;
     const uint64_t tile = 32ull * streams * a.run;
     const uint64_t ntiles = (r.count + tile - 1) / tile;
-    const int warps_per_block = kHeadThreads / 32;
-    const int occ = head_occupancy(r.path, streams, lmax);
+    const int warps_per_block = p->cta / 32;
+    const int occ = head_occupancy(r.path, streams, lmax, p->cta);
     const uint64_t want = (ntiles + warps_per_block - 1) / warps_per_block;
     const int blocks = static_cast<int>(std::max<uint64_t>(1, std::min<uint64_t>(want, uint64_t(occ) * p->sm_count)));
     if (p->profile) BBP_CUDA(cudaEventRecord(p->ev0, st));
-    BBP_CUDA(launch_head(a, r.path, streams, lmax, blocks, st));
+    BBP_CUDA(launch_head(a, r.path, streams, lmax, blocks, st, p->cta));
     if (p->profile) {
       BBP_CUDA(cudaEventRecord(p->ev1, st));
       BBP_CUDA(cudaEventSynchronize(p->ev1));
@@ -241,14 +241,14 @@ bbp_status launch_ranges(bbp_plan p, int f, uint64_t n, uint32_t W, const std::v
   return BBP_OK;
 }
 
-bbp_status plan_query(int f, uint64_t n, uint32_t W, int j_only, uint64_t k_lo, uint64_t k_hi,
+bbp_status plan_query(bbp_plan p, int f, uint64_t n, uint32_t W, int j_only, uint64_t k_lo, uint64_t k_hi,
                       std::vector<TermRange>& ranges, uint64_t* n_terms) {
   const FormulaDef& F = formula_def(f);
-  const int lmax = head_lmax_for(static_cast<int>(W / 32));
+  const int lmax = pick_lmax(W, p->limb_bump);
   uint64_t N = 0;
   for (uint32_t j = 0; j < F.count; ++j) {
     if (j_only >= 0 && static_cast<int>(j) != j_only) continue;
-    const int st = plan_series(F, j, n, W, static_cast<uint32_t>(lmax), k_lo, k_hi, ranges);
+    const int st = plan_series(F, j, n, W, static_cast<uint32_t>(lmax), k_lo, k_hi, ranges, p->wide_min_bits);
     if (st == -6) return BBP_ERANGE;
     if (st != 0) return BBP_EINVAL;
     N += natural_end(F, j, n - 1, W);
@@ -268,7 +268,7 @@ bbp_status bbp_partial_sum_async(bbp_plan p, bbp_formula f, uint32_t denominator
   uint32_t W;
   if (!working_bits(P, p->guard, &W)) return BBP_EINVAL;
   std::vector<TermRange> ranges;
-  const bbp_status st = plan_query(f, n, W, static_cast<int>(denominator), k_begin, k_end, ranges, nullptr);
+  const bbp_status st = plan_query(p, f, n, W, static_cast<int>(denominator), k_begin, k_end, ranges, nullptr);
   if (st != BBP_OK) return st;
   BBP_CUDA(cudaSetDevice(p->device));
   cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : p->stream;
@@ -300,7 +300,7 @@ bbp_status bbp_bits_async(bbp_plan p, bbp_formula f, uint64_t n, uint32_t P, uin
   if (!working_bits(P, p->guard, &W)) return BBP_EINVAL;
   std::vector<TermRange> ranges;
   uint64_t N = 0;
-  const bbp_status st = plan_query(f, n, W, -1, 0, UINT64_MAX, ranges, &N);
+  const bbp_status st = plan_query(p, f, n, W, -1, 0, UINT64_MAX, ranges, &N);
   if (st != BBP_OK) return st;
   BBP_CUDA(cudaSetDevice(p->device));
   cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : p->stream;
@@ -337,7 +337,7 @@ bbp_status bbp_accumulate_async(bbp_plan p, bbp_formula f, uint64_t n, uint32_t 
   for (uint32_t j = 0; j < F.count; ++j) {
     uint64_t kb, ke;
     shard_range(F, j, n, W, shard, nshards, &kb, &ke);
-    const bbp_status st = plan_query(f, n, W, static_cast<int>(j), kb, ke, ranges, nullptr);
+    const bbp_status st = plan_query(p, f, n, W, static_cast<int>(j), kb, ke, ranges, nullptr);
     if (st != BBP_OK) return st;
   }
   BBP_CUDA(cudaSetDevice(p->device));

@@ -23,6 +23,9 @@ struct bbp_plan_s {
   int run = 64;
   int streams = 1;
   int grab = 4;  // batched pass: warp tiles handed out per queue operation
+  int cta = 256;  // single-query head launches: threads per CTA (multiple of 32, <= 256)
+  int limb_bump = 0;  // single-query head launches: accumulator limb class this many sizes above the smallest
+  int wide_min_bits = bbp::kWideMinBits;  // moduli of at least this many bits take the 64-bit Montgomery path
   // single-query buffers
   unsigned long long* d_slots = nullptr;  // kMaxLimbs carry-save accumulators
   uint32_t* d_limbs = nullptr;
@@ -39,7 +42,7 @@ struct bbp_plan_s {
 namespace bbp {
 
 bbp_status cuda_status(cudaError_t e);
-bbp_status plan_query(int f, uint64_t n, uint32_t W, int j_only, uint64_t k_lo, uint64_t k_hi,
+bbp_status plan_query(bbp_plan p, int f, uint64_t n, uint32_t W, int j_only, uint64_t k_lo, uint64_t k_hi,
                       std::vector<TermRange>& ranges, uint64_t* n_terms);
 bbp_status launch_ranges(bbp_plan p, int f, uint64_t n, uint32_t W, const std::vector<TermRange>& ranges,
                          unsigned long long* slots, cudaStream_t st);

@@ -174,7 +174,7 @@ bbp_status plan_query_work(bbp_plan p, uint64_t n, uint32_t P, Query* q) {
   std::vector<TermRange> ranges;
   uint64_t N = 0;
   for (uint32_t j = 0; j < F.count; ++j) {
-    const int st = plan_series(F, j, n, W, static_cast<uint32_t>(lmax), 0, UINT64_MAX, ranges);
+    const int st = plan_series(F, j, n, W, static_cast<uint32_t>(lmax), 0, UINT64_MAX, ranges, p->wide_min_bits);
     if (st == -6) return BBP_ERANGE;
     if (st != 0) return BBP_EINVAL;
     N += natural_end(F, j, n - 1, W);

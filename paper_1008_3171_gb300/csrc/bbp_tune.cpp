@@ -1,6 +1,7 @@
 // Autotune table loading: a small JSON object written by the autotuner
-// (paper_1008_3171_gb300/autotune.py), e.g. {"run": 32, "streams": 1, "grab": 8}.
-// Unknown keys are ignored; missing keys keep the built-in defaults.
+// (paper_1008_3171_gb300/autotune.py), e.g. {"run": 32, "streams": 1, "grab": 8,
+// "cta": 256, "limb_bump": 0, "wide_min_bits": 30}.  Unknown keys are ignored;
+// missing or out-of-range values keep the built-in defaults.
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -37,6 +38,9 @@ void load_tune_table(bbp_plan p, const char* path) {
   if (read_int(text, "run", &v) && v >= 2 && v <= 4096 && v % 2 == 0) p->run = static_cast<int>(v);
   if (read_int(text, "streams", &v) && (v == 1 || v == 2)) p->streams = static_cast<int>(v);
   if (read_int(text, "grab", &v) && v >= 1 && v <= 1024) p->grab = static_cast<int>(v);
+  if (read_int(text, "cta", &v) && v >= 32 && v <= 256 && v % 32 == 0) p->cta = static_cast<int>(v);
+  if (read_int(text, "limb_bump", &v) && v >= 0 && v <= 2) p->limb_bump = static_cast<int>(v);
+  if (read_int(text, "wide_min_bits", &v) && v >= 2 && v <= kWideMinBits) p->wide_min_bits = static_cast<int>(v);
 }
 
 }  // namespace bbp

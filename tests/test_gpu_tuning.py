@@ -1,6 +1,8 @@
 """Every launch configuration the autotuner can pick computes the same exact sums:
-terms per run, pairs per thread (1 or 2 streams) and queue hand-out size change
-only the schedule, never a bit of the result."""
+terms per run, pairs per thread (1 or 2 streams), CTA size, accumulator limb
+class, the Montgomery width crossover (small moduli on the two-limb path) and
+queue hand-out size change only the schedule or the arithmetic route, never a
+bit of the result."""
 
 import json
 import os
@@ -18,6 +20,9 @@ SETTINGS = [
     {"run": 16, "streams": 2, "grab": 3},
     {"run": 64, "streams": 1, "grab": 32},
     {"run": 128, "streams": 2, "grab": 8},
+    {"run": 64, "cta": 64, "limb_bump": 1, "wide_min_bits": 2},
+    {"run": 32, "streams": 2, "cta": 128, "wide_min_bits": 17, "grab": 2},
+    {"run": 64, "cta": 32, "limb_bump": 2, "wide_min_bits": 29},
 ]
 
 
@@ -47,3 +52,21 @@ def test_settings_give_identical_sums(setting):
             assert (vals[q], valid[q]) == oracle.c_bits(n, P, 64)
     finally:
         p.close()
+
+
+def test_montgomery_width_setting_is_applied():
+    """Moduli below 2^20 move to the two-limb path when wide_min_bits = 2: the
+    result is unchanged and the modelled multiply count rises (13 instead of 4
+    halves per squaring)."""
+    import paper_1008_3171_gb300 as bbp
+
+    default = plan_with(bbp, {})
+    wide = plan_with(bbp, {"wide_min_bits": 2})
+    try:
+        assert default.bits(10**6, 64) == wide.bits(10**6, 64) == oracle.c_bits(10**6, 64, 64)
+        d, w = default.stats(), wide.stats()
+        assert d["terms"] == w["terms"]
+        assert w["imad_model"] > 1.5 * d["imad_model"]
+    finally:
+        default.close()
+        wide.close()
