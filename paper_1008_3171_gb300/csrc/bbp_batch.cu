@@ -30,12 +30,11 @@ using namespace bbp;
 
 namespace {
 
-constexpr int kLmaxClasses[] = {3, 4, 6, 10, 16, 40};
-constexpr int kVariants = 6 * 3;
+constexpr int kVariants = kQueueVariants;
 constexpr uint32_t kOutStride = kMaxWorkingBits / 8;  // bytes of output per query slot
 
 int lmax_index(int lmax) {
-  for (int i = 0; i < 6; ++i)
+  for (int i = 0; i < kNumLmaxClasses; ++i)
     if (kLmaxClasses[i] == lmax) return i;
   return -1;
 }

@@ -538,7 +538,6 @@ __global__ void imad_probe_kernel(int iters, unsigned long long* cycles, uint32_
 // ---------------------------------------------------------------- launchers
 
 namespace {
-constexpr int kLmaxList[] = {3, 4, 6, 10, 16, 40};
 
 template <int LMAX, int PATH, int S>
 cudaError_t launch_head_t(const HeadArgs& a, int blocks, int threads, cudaStream_t s) {
@@ -592,6 +591,7 @@ int head_occupancy(int path, int streams, int lmax, int threads) {
     case 6: return occupancy_l<6>(path, streams, threads);
     case 10: return occupancy_l<10>(path, streams, threads);
     case 16: return occupancy_l<16>(path, streams, threads);
+    case 24: return occupancy_l<24>(path, streams, threads);
     case 40: return occupancy_l<40>(path, streams, threads);
     default: return 1;
   }
@@ -642,6 +642,7 @@ int queue_occupancy(int path, int streams, int lmax) {
     case 6: return queue_occupancy_l<6>(path, streams);
     case 10: return queue_occupancy_l<10>(path, streams);
     case 16: return queue_occupancy_l<16>(path, streams);
+    case 24: return queue_occupancy_l<24>(path, streams);
     case 40: return queue_occupancy_l<40>(path, streams);
     default: return 1;
   }
@@ -655,6 +656,7 @@ cudaError_t launch_queue(const BatchDev& b, uint32_t job_begin, uint32_t job_end
     case 6: return launch_queue_l<6>(b, job_begin, job_end, cursor, path, streams, blocks, s);
     case 10: return launch_queue_l<10>(b, job_begin, job_end, cursor, path, streams, blocks, s);
     case 16: return launch_queue_l<16>(b, job_begin, job_end, cursor, path, streams, blocks, s);
+    case 24: return launch_queue_l<24>(b, job_begin, job_end, cursor, path, streams, blocks, s);
     case 40: return launch_queue_l<40>(b, job_begin, job_end, cursor, path, streams, blocks, s);
     default: return cudaErrorInvalidValue;
   }
@@ -673,9 +675,8 @@ cudaError_t launch_queue_tail(const BatchDev& b, uint32_t tail_begin, uint32_t t
 }
 
 int head_lmax_for(int L, int bump) {
-  constexpr int n = static_cast<int>(sizeof(kLmaxList) / sizeof(kLmaxList[0]));
-  for (int i = 0; i < n; ++i)
-    if (kLmaxList[i] >= L) return kLmaxList[std::min(n - 1, i + std::max(0, bump))];
+  for (int i = 0; i < kNumLmaxClasses; ++i)
+    if (kLmaxClasses[i] >= L) return kLmaxClasses[std::min(kNumLmaxClasses - 1, i + std::max(0, bump))];
   return 0;
 }
 
@@ -687,6 +688,7 @@ cudaError_t launch_head(const HeadArgs& a, int path, int streams, int lmax, int 
     case 6: return launch_head_l<6>(a, path, streams, blocks, threads, s);
     case 10: return launch_head_l<10>(a, path, streams, blocks, threads, s);
     case 16: return launch_head_l<16>(a, path, streams, blocks, threads, s);
+    case 24: return launch_head_l<24>(a, path, streams, blocks, threads, s);
     case 40: return launch_head_l<40>(a, path, streams, blocks, threads, s);
     default: return cudaErrorInvalidValue;
   }

@@ -42,6 +42,11 @@ struct TailArgs {
 
 constexpr int kMaxLimbs = 40;    // W <= 1280 bits
 constexpr int kHeadThreads = 256;
+// Compiled accumulator capacities (limbs per thread) of the head and queue
+// kernels; a query with W/32 limbs uses the smallest class that holds them.
+constexpr int kLmaxClasses[] = {3, 4, 6, 10, 16, 24, 40};
+constexpr int kNumLmaxClasses = static_cast<int>(sizeof(kLmaxClasses) / sizeof(kLmaxClasses[0]));
+constexpr int kQueueVariants = kNumLmaxClasses * 3;  // limb class x modulus path
 
 // ---------------------------------------------------------------- batches
 //

@@ -37,14 +37,13 @@ using namespace bbp;
 
 namespace {
 
-constexpr int kLmaxClasses[] = {3, 4, 6, 10, 16, 40};
-constexpr int kVariants = 6 * 3;
+constexpr int kVariants = kQueueVariants;
 constexpr uint32_t kOutStride = kMaxWorkingBits / 8;
 constexpr double kIterTargetSeconds = 0.025;  // target duration of one iteration
 constexpr double kInitialRate = 2.0e10;       // terms/s before the first measurement
 
 int lmax_index(int lmax) {
-  for (int i = 0; i < 6; ++i)
+  for (int i = 0; i < kNumLmaxClasses; ++i)
     if (kLmaxClasses[i] == lmax) return i;
   return -1;
 }
@@ -478,18 +477,22 @@ bool finish_iteration(ServeEngine* E, HostStage& H) {
   return true;
 }
 
+// An iteration could not be enqueued or did not complete: every admitted query
+// fails (bbp_poll returns BBP_ECUDA) and gives its slot back, so that later
+// submissions are admitted again (a fresh slot is zeroed on admission).
 void fail_all(ServeEngine* E) {
   std::lock_guard<std::mutex> lock(E->mu);
-  for (Query* q : E->stage.finishing) {
+  auto fail = [&](Query* q) {
     q->state = kFailed;
     q->error = BBP_ECUDA;
-  }
+    if (q->slot >= 0) E->free_slots.push_back(q->slot);
+    q->slot = -1;
+    q->work.clear();
+  };
+  for (Query* q : E->stage.finishing) fail(q);
   E->stage.finishing.clear();
   E->stage.in_flight = false;
-  for (Query* q : E->active) {
-    q->state = kFailed;
-    q->error = BBP_ECUDA;
-  }
+  for (Query* q : E->active) fail(q);
   E->active.clear();
 }
 

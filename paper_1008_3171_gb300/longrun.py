@@ -113,7 +113,7 @@ def run(n: int, P: int, shards: int, checkpoint: str = "", formula: int = 0, gua
         max_seconds: float = float("inf"), max_shards: int = -1, device: int = 0) -> dict:
     """Adds the shards that `checkpoint` does not hold yet, saving after each one,
     until all are in, `max_shards` were added or `max_seconds` would be passed
-    (judged from the slowest shard so far); then finalizes if complete."""
+    (estimated from the slowest shard so far); then finalizes if complete."""
     import torch
 
     from . import Plan

@@ -239,3 +239,16 @@ def test_strict_mode(bbp):
         assert p.bits(9, 8) == (0x3F, 8)
     finally:
         p.close()
+
+
+@pytest.mark.parametrize("P", [64, 96, 160, 288, 448, 512, 736, 1000, 1216])
+def test_every_limb_class_matches_oracle(plan64, P):
+    """W = roundup(P, 32) + 64 from 4 to 40 limbs: every compiled accumulator class
+    (3, 4, 6, 10, 16, 24, 40 limbs), its lower and upper fill, on both modulus
+    paths (a 64-bit-modulus slice of n = 1e12) and in whole queries."""
+    assert plan64.bits(123_457, P) == oracle.c_bits(123_457, P, 64)
+    assert plan64.bits(10**7 + 1, P) == oracle.c_bits(10**7 + 1, P, 64)
+    for j in (0, 6):
+        kb = 31 * 10**9 + 17
+        got = plan64.partial_sum(0, j, kb, kb + 40_001, 10**12, P)
+        assert got == oracle.c_partial_sum(0, j, kb, kb + 40_001, 10**12, P, 64), (P, j)
