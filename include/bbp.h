@@ -62,7 +62,13 @@ typedef struct bbp_plan_opts {
   uint32_t guard_bits;      /* G: positive multiple of 32; 0 selects 64 */
   size_t accum_mem_budget;  /* bytes of device accumulator memory for queued queries; 0: 64 MiB */
   uint32_t max_slots;       /* concurrent queries admitted by bbp_submit; 0: 4096 */
-  const char* tune_table;   /* path of an autotune table (JSON: run, streams, grab) or NULL for defaults */
+  const char* tune_table;   /* path of an autotune table or NULL for defaults.  JSON object; keys (others
+                               ignored, out-of-range values keep the default): run (even, 2..4096, terms
+                               per stream; 64), streams (1 or 2; 1), cta (head-kernel threads per CTA,
+                               multiple of 32 up to 256; 256), limb_bump (0..2 accumulator classes above
+                               the smallest that holds W; 0), wide_min_bits (2..30: moduli of at least
+                               this many bits use the two-limb Montgomery path; 30), grab (1..1024 warp
+                               tiles per queue operation in batched passes; 4).  None changes a result. */
   uint32_t profile;         /* 1: time head-kernel launches with CUDA events (see bbp_stats) */
   uint32_t strict;          /* 1: bbp_bits fails with BBP_EINVALID_BITS unless all P bits certify */
 } bbp_plan_opts;
