@@ -143,6 +143,32 @@ bbp_status bbp_bits_async(bbp_plan p, bbp_formula f, uint64_t n, uint32_t P, uin
 bbp_status bbp_shard_range(bbp_formula f, uint32_t denominator, uint64_t n, uint32_t W, uint32_t shard,
                            uint32_t nshards, uint64_t* k_begin, uint64_t* k_end);
 
+/* One launch range of a query plan (bbp_explain). */
+typedef struct bbp_range {
+  uint32_t denominator;  /* series index j */
+  uint32_t tail;         /* 0: head terms (exponent >= 0, modular exponentiation), 1: tail terms */
+  uint32_t path;         /* head: 0 one-limb (32-bit) Montgomery, 1 two-limb for moduli < 2^47, 2 two-limb < 2^60 */
+  uint32_t window;       /* head: ladder window bits (a window's multiplication is a shift) */
+  uint32_t first;        /* head: bits taken by the first window (no squaring) */
+  uint32_t reserved;
+  uint64_t k_begin;      /* first k */
+  uint64_t count;        /* number of terms */
+  double imad;           /* modelled 32-bit multiply halves of the range (head only; see bbp_stats) */
+} bbp_range;
+
+/* Host-only plan of the whole query at bit position n with P bits and guard_bits
+ * guard bits (W = roundup(P, 32) + guard_bits): the launch ranges bbp_bits would
+ * run, series by series in k order, with the moduli of at least wide_min_bits
+ * bits (2..30; 30 is the default plan) on the two-limb path.  Head terms with
+ * modulus 1 (their value is 0) are not in any range.  Writes min(*count, cap)
+ * ranges to `out` (caller-owned, may be NULL when cap = 0), sets *count to the
+ * number of ranges and *terms (may be NULL) to the number of terms they cover.
+ * Needs no GPU.  EINVAL: bad formula, n = 0, P = 0, guard_bits not a positive
+ * multiple of 32, W > 1280, wide_min_bits outside 2..30; ERANGE: a modulus
+ * would reach 2^60. */
+bbp_status bbp_explain(bbp_formula f, uint64_t n, uint32_t P, uint32_t guard_bits, uint32_t wide_min_bits,
+                       bbp_range* out, uint32_t cap, uint32_t* count, uint64_t* terms);
+
 /* Adds shard `shard` of `nshards` of the whole query (every series, ranges from
  * bbp_shard_range) into caller-owned device carry-save accumulators
  * d_slots[0..W/32): limb i of the signed sum is added to d_slots[i] (uint64).

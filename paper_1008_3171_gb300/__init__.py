@@ -66,6 +66,20 @@ class bbp_serve_info(ctypes.Structure):
     ]
 
 
+class bbp_range(ctypes.Structure):
+    _fields_ = [
+        ("denominator", ctypes.c_uint32),
+        ("tail", ctypes.c_uint32),
+        ("path", ctypes.c_uint32),
+        ("window", ctypes.c_uint32),
+        ("first", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
+        ("k_begin", ctypes.c_uint64),
+        ("count", ctypes.c_uint64),
+        ("imad", ctypes.c_double),
+    ]
+
+
 class bbp_stats(ctypes.Structure):
     _fields_ = [
         ("terms", ctypes.c_uint64),
@@ -108,6 +122,8 @@ def _load():
         "bbp_bits_async": ([vp, ctypes.c_int, u64, u32, vp, vp, vp, vp], ctypes.c_int),
         "bbp_plan_stats": ([vp, ctypes.POINTER(bbp_stats)], ctypes.c_int),
         "bbp_shard_range": ([ctypes.c_int, u32, u64, u32, u32, u32, u64p, u64p], ctypes.c_int),
+        "bbp_explain": ([ctypes.c_int, u64, u32, u32, u32, ctypes.POINTER(bbp_range), u32, u32p, u64p],
+                        ctypes.c_int),
         "bbp_accumulate_async": ([vp, ctypes.c_int, u64, u32, u32, u32, vp, vp], ctypes.c_int),
         "bbp_finalize_async": ([vp, ctypes.c_int, u64, u32, vp, vp, vp, vp, vp], ctypes.c_int),
         "bbp_imad_probe": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
@@ -222,6 +238,19 @@ def bbp_shard_range(formula: int, denominator: int, n: int, W: int, shard: int, 
     _check(_lib.bbp_shard_range(formula, denominator, n, W, shard, nshards, ctypes.byref(kb), ctypes.byref(ke)),
            "bbp_shard_range")
     return kb.value, ke.value
+
+
+def bbp_explain(formula: int, n: int, P: int, guard_bits: int = 64, wide_min_bits: int = 30) -> tuple[list, int]:
+    """Host-only launch plan of a query: (ranges as dicts, terms covered).  No GPU."""
+    count = ctypes.c_uint32()
+    terms = ctypes.c_uint64()
+    _check(_lib.bbp_explain(formula, n, P, guard_bits, wide_min_bits, None, 0, ctypes.byref(count), None),
+           "bbp_explain")
+    buf = (bbp_range * max(count.value, 1))()
+    _check(_lib.bbp_explain(formula, n, P, guard_bits, wide_min_bits, buf, count.value, ctypes.byref(count),
+                            ctypes.byref(terms)), "bbp_explain")
+    names = [f for f, _ in bbp_range._fields_ if f != "reserved"]
+    return [{f: getattr(buf[i], f) for f in names} for i in range(count.value)], terms.value
 
 
 def bbp_accumulate_async(plan: int, formula: int, n: int, P: int, shard: int, nshards: int, d_slots: int,

@@ -326,6 +326,44 @@ bbp_status bbp_shard_range(bbp_formula f, uint32_t denominator, uint64_t n, uint
   return BBP_OK;
 }
 
+bbp_status bbp_explain(bbp_formula f, uint64_t n, uint32_t P, uint32_t guard_bits, uint32_t wide_min_bits,
+                       bbp_range* out, uint32_t cap, uint32_t* count, uint64_t* terms) {
+  uint32_t W;
+  if (!valid_formula(f) || n == 0 || !count || (cap > 0 && !out) || !working_bits(P, guard_bits, &W))
+    return BBP_EINVAL;
+  if (wide_min_bits < 2 || wide_min_bits > static_cast<uint32_t>(kWideMinBits)) return BBP_EINVAL;
+  const FormulaDef& F = formula_def(f);
+  const int lmax = head_lmax_for(static_cast<int>(W / 32));
+  if (lmax == 0) return BBP_EINVAL;
+  std::vector<TermRange> ranges;
+  for (uint32_t j = 0; j < F.count; ++j) {
+    const int st = plan_series(F, j, n, W, static_cast<uint32_t>(lmax), 0, UINT64_MAX, ranges,
+                               static_cast<int>(wide_min_bits));
+    if (st == -6) return BBP_ERANGE;
+    if (st != 0) return BBP_EINVAL;
+  }
+  uint64_t total = 0;
+  for (size_t i = 0; i < ranges.size(); ++i) {
+    const TermRange& r = ranges[i];
+    total += r.count;
+    if (i < cap) {
+      bbp_range& o = out[i];
+      o.denominator = r.j;
+      o.tail = r.tail;
+      o.path = r.path;
+      o.window = r.window;
+      o.first = r.first;
+      o.reserved = 0;
+      o.k_begin = r.k_begin;
+      o.count = r.count;
+      o.imad = r.imad;
+    }
+  }
+  *count = static_cast<uint32_t>(ranges.size());
+  if (terms) *terms = total;
+  return BBP_OK;
+}
+
 bbp_status bbp_accumulate_async(bbp_plan p, bbp_formula f, uint64_t n, uint32_t P, uint32_t shard, uint32_t nshards,
                                 unsigned long long* d_slots, void* stream) {
   if (!p || !valid_formula(f) || n == 0 || P == 0 || !d_slots || nshards == 0 || shard >= nshards)

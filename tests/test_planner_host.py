@@ -1,0 +1,156 @@
+"""Host-side launch planning (bbp_explain, no GPU): for many positions, widths and
+Montgomery crossovers, the ranges a query launches cover exactly the terms of
+the definition, and every head range satisfies the bounds its kernel's
+arithmetic needs.
+
+Coverage is checked against the oracle's own series extents (Eq. 4 split, tail
+end by truncation).  The bounds come from the Montgomery ladder the kernels run
+(R = 2^64 on two limbs, 2^32 on one; lazy residues x < 2m; REDC of T returns a
+value below 2m when T < m R):
+  * a squaring with the window's value s shifted in reduces x^2 2^s < 4 m^2 2^s,
+    so 4 m 2^s < R for every shift the window can produce, s <= 2^window - 1;
+  * the first window starts from x = (R mod m) << w0 < m 2^w0 with w0 < 2^first,
+    and the first squaring after it carries a shift of at most one bit, so
+    m 2^(2 w0 + 1) < R;
+  * the two-limb path that keeps only the low word of x1^2 (path 1) needs
+    x < 2^48 after the first window, and x < 2m < 2^48 after every reduction;
+  * the one-limb path needs m < 2^29 (a residue below 2m and its shifted square
+    stay within the 32-bit bounds above), the two-limb paths m < 2^60.
+"""
+
+import importlib.util
+import math
+import os
+import random
+
+import pytest
+
+from conftest import ROOT
+from oracle import bbp_oracle as o1
+
+
+@pytest.fixture(scope="module")
+def bbp():
+    spec = importlib.util.spec_from_file_location("_bbp_build", os.path.join(ROOT, "paper_1008_3171_gb300", "_build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    mod.build()
+    import paper_1008_3171_gb300 as m
+
+    return m
+
+
+def _positions():
+    rng = random.Random(2024)
+    ns = [1, 2, 3, 5, 9, 10, 11, 17, 100, 1001, 4096, 65537, 10**6, 10**9 + 1, 10**12, 10**13 + 1,
+          10**14 + 1, 2 * 10**15 - 3, 10**16 + 7]
+    ns += [int(10 ** rng.uniform(0, 16.5)) or 1 for _ in range(24)]
+    return ns
+
+
+CASES = [(f, n, P, G, wide)
+         for f in (0, 1)
+         for n in _positions()
+         for P, G in ((1, 32), (64, 32), (256, 64), (1000, 64))
+         for wide in (2, 17, 30)]
+
+
+def _check_plan(bbp, f, n, P, G, wide):
+    ranges, terms = bbp.bbp_explain(f, n, P, G, wide)
+    F = o1.FORMULAS[f]
+    W = o1.working_bits(P, G)
+    d = n - 1
+    total = 0
+    for j, s in enumerate(F.series):
+        mine = [r for r in ranges if r["denominator"] == j]
+        he = o1.head_end(F, s, d)
+        ne = o1.natural_end(F, s, d, W)
+        # heads first, then at most one tail range; contiguous, in k order
+        k = 1 if (s.b == 1 and he > 0) else 0          # the m = 1 head term is 0 and is skipped
+        seen_tail = False
+        for r in mine:
+            assert r["count"] > 0
+            assert r["k_begin"] == k, (f, n, P, G, wide, j, r)
+            k = r["k_begin"] + r["count"]
+            if r["tail"]:
+                assert not seen_tail and r["k_begin"] == he
+                seen_tail = True
+            else:
+                assert not seen_tail and k <= he
+                _check_head_bounds(s, r, wide, W, d, F)
+        assert k == ne, (f, n, j, k, he, ne)            # ne >= he: the tail, if any, ends the series
+        assert seen_tail == (ne > he)
+        expected = ne - (1 if (s.b == 1 and he > 0) else 0)
+        assert sum(r["count"] for r in mine) == expected
+        total += expected
+    assert terms == total
+
+
+def _check_head_bounds(s, r, wide, W, d, F):
+    k_last = r["k_begin"] + r["count"] - 1
+    m_max = s.a * k_last + s.b
+    m_min = s.a * r["k_begin"] + s.b
+    assert m_min >= 3 and m_min % 2 == 1
+    path, window, first = r["path"], r["window"], r["first"]
+    R = 1 << (64 if path else 32)
+    if path == 0:
+        assert m_max < 1 << 29 and m_max.bit_length() < wide
+    elif path == 1:
+        assert m_max < 1 << 47 and m_min.bit_length() >= min(wide, 30)
+    else:
+        assert m_max < 1 << 60 and m_min.bit_length() >= 48
+    assert 1 <= window
+    assert 4 * m_max * (1 << ((1 << window) - 1)) < R                  # shifted squarings
+    if first:
+        w0 = (1 << first) - 1
+        assert m_max * (1 << (2 * w0 + 1)) < R                          # first squaring after the first window
+        if path == 1:
+            assert m_max * (1 << w0) <= 1 << 48                         # x1^2 fits one word
+    # every head term's exponent is >= 0, so the ladder exponent e + W >= W >= R's width
+    e_last = d + s.c - F.step * k_last
+    assert e_last >= 0 and e_last + W >= (64 if path else 32)
+    assert r["imad"] > 0
+
+
+@pytest.mark.parametrize("n", _positions())
+def test_plan_covers_every_term_within_kernel_bounds(bbp, n):
+    for f, n_, P, G, wide in CASES:
+        if n_ == n:
+            _check_plan(bbp, f, n, P, G, wide)
+
+
+def test_default_headline_plan(bbp):
+    """n = 1e12, P = 256, G = 64: 42 head launches (moduli from 3 to 2^40) and 7
+    tail launches, 7e11 terms; the 64-bit ranges carry almost all of them."""
+    ranges, terms = bbp.bbp_explain(0, 10**12, 256, 64, 30)
+    heads = [r for r in ranges if not r["tail"]]
+    assert len(heads) == 42 and len(ranges) - len(heads) == 7
+    assert terms == 700_000_000_195
+    wide = sum(r["count"] for r in heads if r["path"] > 0)
+    assert wide / terms > 0.999
+
+
+def test_crossover_moves_small_moduli_to_two_limbs(bbp):
+    for wide in (2, 10, 20, 30):
+        ranges, _ = bbp.bbp_explain(0, 10**7 + 1, 64, 64, wide)
+        for r in ranges:
+            if not r["tail"]:
+                s = o1.BELLARD.series[r["denominator"]]
+                m_max = s.a * (r["k_begin"] + r["count"] - 1) + s.b
+                assert (r["path"] == 0) == (m_max.bit_length() < wide)
+
+
+def test_errors(bbp):
+    with pytest.raises(bbp.BBPError) as e:
+        bbp.bbp_explain(0, 0, 64)
+    assert e.value.status == bbp.BBP_EINVAL
+    for args in ((0, 100, 0, 64, 30), (0, 100, 64, 0, 30), (0, 100, 64, 48, 30), (0, 100, 1250, 64, 30),
+                 (0, 100, 64, 64, 1), (0, 100, 64, 64, 31), (2, 100, 64, 64, 30)):
+        with pytest.raises(bbp.BBPError) as e:
+            bbp.bbp_explain(*args)
+        assert e.value.status == bbp.BBP_EINVAL, args
+    # a modulus reaching 2^60: n about 2^62 for Bellard's 4k + 1 series
+    with pytest.raises(bbp.BBPError) as e:
+        bbp.bbp_explain(0, 1 << 62, 64)
+    assert e.value.status == bbp.BBP_ERANGE
+    assert math.isfinite(bbp.bbp_explain(0, 1 << 40, 64)[0][0]["imad"])
