@@ -66,7 +66,7 @@ typedef struct bbp_plan_opts {
                                ignored, out-of-range values keep the default): run (even, 2..4096, terms
                                per stream; 64), streams (1 or 2; 1), cta (head-kernel threads per CTA,
                                multiple of 32 up to 256; 256), limb_bump (0..2 accumulator classes above
-                               the smallest that holds W; 0), wide_min_bits (2..30: moduli of at least
+                               the smallest that holds W; 0), wide_min_bits (5..30: moduli of at least
                                this many bits use the two-limb Montgomery path; 30), grab (1..1024 warp
                                tiles per queue operation in batched passes; 4).  None changes a result. */
   uint32_t profile;         /* 1: time head-kernel launches with CUDA events (see bbp_stats) */
@@ -159,12 +159,12 @@ typedef struct bbp_range {
 /* Host-only plan of the whole query at bit position n with P bits and guard_bits
  * guard bits (W = roundup(P, 32) + guard_bits): the launch ranges bbp_bits would
  * run, series by series in k order, with the moduli of at least wide_min_bits
- * bits (2..30; 30 is the default plan) on the two-limb path.  Head terms with
+ * bits (5..30; 30 is the default plan) on the two-limb path.  Head terms with
  * modulus 1 (their value is 0) are not in any range.  Writes min(*count, cap)
  * ranges to `out` (caller-owned, may be NULL when cap = 0), sets *count to the
  * number of ranges and *terms (may be NULL) to the number of terms they cover.
  * Needs no GPU.  EINVAL: bad formula, n = 0, P = 0, guard_bits not a positive
- * multiple of 32, W > 1280, wide_min_bits outside 2..30; ERANGE: a modulus
+ * multiple of 32, W > 1280, wide_min_bits outside 5..30; ERANGE: a modulus
  * would reach 2^60. */
 bbp_status bbp_explain(bbp_formula f, uint64_t n, uint32_t P, uint32_t guard_bits, uint32_t wide_min_bits,
                        bbp_range* out, uint32_t cap, uint32_t* count, uint64_t* terms);

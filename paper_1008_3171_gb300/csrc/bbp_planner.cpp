@@ -127,7 +127,7 @@ double range_imad(const FormulaDef& f, const SeriesDef& s, uint64_t d, uint32_t 
 int plan_series(const FormulaDef& f, uint32_t j, uint64_t n, uint32_t W, uint32_t lmax, uint64_t k_lo,
                 uint64_t k_hi, std::vector<TermRange>& out, int wide_min_bits) {
   if (n == 0 || j >= f.count || W == 0 || W % 32 != 0 || W > kMaxWorkingBits) return -1;
-  if (wide_min_bits < 2 || wide_min_bits > kWideMinBits) return -1;
+  if (wide_min_bits < kWideFloorBits || wide_min_bits > kWideMinBits) return -1;
   const SeriesDef& s = f.s[j];
   const uint64_t d = n - 1;
   const uint64_t he = head_end(f, j, d);

@@ -25,6 +25,10 @@ const FormulaDef& formula_def(int f);
 
 constexpr uint32_t kMaxWorkingBits = 1280;   // 40 limbs
 constexpr int kWideMinBits = 30;             // moduli with bitlen >= 30 take a 64-bit path
+// Lowest allowed crossover: moduli on the 64-bit path are >= 2^(kWideFloorBits-1) = 16,
+// so floor(2^64 / m) * a (a <= 10), formed when R mod m is carried to the next k,
+// stays below 2^64.
+constexpr int kWideFloorBits = 5;
 constexpr int kSmallMaxBits = 47;            // 64-bit path 1 (x1^2 < 2^32) up to this bitlen
 constexpr int kMaxModulusBits = 60;          // 64-bit path bound
 
@@ -51,7 +55,8 @@ uint64_t natural_end(const FormulaDef& f, uint32_t j, uint64_t d, uint32_t W);
 
 // Kernel path for moduli of `lbits` bits: 0 (32-bit Montgomery) below
 // `wide_min_bits`, else 1 or 2 (64-bit).  wide_min_bits may be lowered from
-// kWideMinBits (a tuning choice: small moduli on the 64-bit path) but not raised.
+// kWideMinBits down to kWideFloorBits (a tuning choice: small moduli on the 64-bit
+// path) but not raised.
 int path_for_bits(int lbits, int wide_min_bits = kWideMinBits);
 
 // Ladder parameters for moduli of at most `lbits` bits on the given path.
@@ -73,7 +78,7 @@ void shard_range(const FormulaDef& f, uint32_t j, uint64_t n, uint32_t W, uint32
 
 // Appends the ranges of series j restricted to k in [k_lo, k_hi) (k_hi = UINT64_MAX:
 // natural end).  Returns 0, or -6 (modulus too large) / -1 (bad argument, including
-// wide_min_bits outside [2, kWideMinBits]).
+// wide_min_bits outside [kWideFloorBits, kWideMinBits]).
 int plan_series(const FormulaDef& f, uint32_t j, uint64_t n, uint32_t W, uint32_t lmax, uint64_t k_lo,
                 uint64_t k_hi, std::vector<TermRange>& out, int wide_min_bits = kWideMinBits);
 

@@ -331,7 +331,8 @@ bbp_status bbp_explain(bbp_formula f, uint64_t n, uint32_t P, uint32_t guard_bit
   uint32_t W;
   if (!valid_formula(f) || n == 0 || !count || (cap > 0 && !out) || !working_bits(P, guard_bits, &W))
     return BBP_EINVAL;
-  if (wide_min_bits < 2 || wide_min_bits > static_cast<uint32_t>(kWideMinBits)) return BBP_EINVAL;
+  if (wide_min_bits < static_cast<uint32_t>(kWideFloorBits) || wide_min_bits > static_cast<uint32_t>(kWideMinBits))
+    return BBP_EINVAL;
   const FormulaDef& F = formula_def(f);
   const int lmax = head_lmax_for(static_cast<int>(W / 32));
   if (lmax == 0) return BBP_EINVAL;

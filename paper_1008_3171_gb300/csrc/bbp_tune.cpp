@@ -40,7 +40,7 @@ void load_tune_table(bbp_plan p, const char* path) {
   if (read_int(text, "grab", &v) && v >= 1 && v <= 1024) p->grab = static_cast<int>(v);
   if (read_int(text, "cta", &v) && v >= 32 && v <= 256 && v % 32 == 0) p->cta = static_cast<int>(v);
   if (read_int(text, "limb_bump", &v) && v >= 0 && v <= 2) p->limb_bump = static_cast<int>(v);
-  if (read_int(text, "wide_min_bits", &v) && v >= 2 && v <= kWideMinBits) p->wide_min_bits = static_cast<int>(v);
+  if (read_int(text, "wide_min_bits", &v) && v >= kWideFloorBits && v <= kWideMinBits) p->wide_min_bits = static_cast<int>(v);
 }
 
 }  // namespace bbp

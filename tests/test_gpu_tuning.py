@@ -20,7 +20,7 @@ SETTINGS = [
     {"run": 16, "streams": 2, "grab": 3},
     {"run": 64, "streams": 1, "grab": 32},
     {"run": 128, "streams": 2, "grab": 8},
-    {"run": 64, "cta": 64, "limb_bump": 1, "wide_min_bits": 2},
+    {"run": 64, "cta": 64, "limb_bump": 1, "wide_min_bits": 5},
     {"run": 32, "streams": 2, "cta": 128, "wide_min_bits": 17, "grab": 2},
     {"run": 64, "cta": 32, "limb_bump": 2, "wide_min_bits": 29},
 ]
@@ -55,13 +55,13 @@ def test_settings_give_identical_sums(setting):
 
 
 def test_montgomery_width_setting_is_applied():
-    """Moduli below 2^20 move to the two-limb path when wide_min_bits = 2: the
+    """Moduli from 2^4 to 2^20 move to the two-limb path when wide_min_bits = 5: the
     result is unchanged and the modelled multiply count rises (13 instead of 4
     halves per squaring)."""
     import paper_1008_3171_gb300 as bbp
 
     default = plan_with(bbp, {})
-    wide = plan_with(bbp, {"wide_min_bits": 2})
+    wide = plan_with(bbp, {"wide_min_bits": 5})
     try:
         assert default.bits(10**6, 64) == wide.bits(10**6, 64) == oracle.c_bits(10**6, 64, 64)
         d, w = default.stats(), wide.stats()

@@ -15,7 +15,8 @@ value below 2m when T < m R):
   * the two-limb path that keeps only the low word of x1^2 (path 1) needs
     x < 2^48 after the first window, and x < 2m < 2^48 after every reduction;
   * the one-limb path needs m < 2^29 (a residue below 2m and its shifted square
-    stay within the 32-bit bounds above), the two-limb paths m < 2^60.
+    stay within the 32-bit bounds above), the two-limb paths m < 2^60;
+  * carrying R mod m along a run forms floor(R / m) * a in 64 bits.
 """
 
 import importlib.util
@@ -52,7 +53,7 @@ CASES = [(f, n, P, G, wide)
          for f in (0, 1)
          for n in _positions()
          for P, G in ((1, 32), (64, 32), (256, 64), (1000, 64))
-         for wide in (2, 17, 30)]
+         for wide in (5, 17, 30)]
 
 
 def _check_plan(bbp, f, n, P, G, wide):
@@ -100,6 +101,8 @@ def _check_head_bounds(s, r, wide, W, d, F):
     else:
         assert m_max < 1 << 60 and m_min.bit_length() >= 48
     assert 1 <= window
+    # R mod m is carried from k to k + 1 with q = floor(R / m): q * a must fit 64 bits
+    assert (R // m_min) * s.a < 1 << 64
     assert 4 * m_max * (1 << ((1 << window) - 1)) < R                  # shifted squarings
     if first:
         w0 = (1 << first) - 1
@@ -131,7 +134,7 @@ def test_default_headline_plan(bbp):
 
 
 def test_crossover_moves_small_moduli_to_two_limbs(bbp):
-    for wide in (2, 10, 20, 30):
+    for wide in (5, 10, 20, 30):
         ranges, _ = bbp.bbp_explain(0, 10**7 + 1, 64, 64, wide)
         for r in ranges:
             if not r["tail"]:
@@ -145,7 +148,7 @@ def test_errors(bbp):
         bbp.bbp_explain(0, 0, 64)
     assert e.value.status == bbp.BBP_EINVAL
     for args in ((0, 100, 0, 64, 30), (0, 100, 64, 0, 30), (0, 100, 64, 48, 30), (0, 100, 1250, 64, 30),
-                 (0, 100, 64, 64, 1), (0, 100, 64, 64, 31), (2, 100, 64, 64, 30)):
+                 (0, 100, 64, 64, 4), (0, 100, 64, 64, 31), (2, 100, 64, 64, 30)):
         with pytest.raises(bbp.BBPError) as e:
             bbp.bbp_explain(*args)
         assert e.value.status == bbp.BBP_EINVAL, args
