@@ -1,0 +1,270 @@
+"""A word-level model of the head kernel's arithmetic, run on the CPU at the
+extremes of the launch ranges the planner produces.
+
+The kernels keep every value in 32-bit words and drop carries they have shown
+cannot occur; the GPU parity tests sample terms, this model checks the claims
+themselves.  It restates, word by word, what the device code does for one term
+(in `csrc/bbp_device.cuh` and `process_tile` in `csrc/bbp_kernels.cu`):
+  * -m^-1 mod 2^32 by Newton-Hensel lifting from m (four steps);
+  * R mod m by bit-serial division, carried to k + 1 with R = q (m + a) + (r - a q);
+  * the left-to-right ladder: a first window taken as (R mod m) << w0, then
+    groups of `window` bits, each len - 1 plain Montgomery squarings and one
+    squaring with the group's bits shifted into the unreduced square;
+  * 64-bit squaring on two words (the x1^2 high word dropped on path 1), the
+    shift by funnel shifts, two word-by-word REDC steps with the vanishing low
+    word's carry taken as (word != 0) and u m1 accumulated by the multiply;
+  * 32-bit squaring and REDC on one word;
+  * W/32 exact-division digits (Hensel), least significant first.
+Every dropped carry, truncated shift and narrowed product is asserted to be
+zero or in range, the ladder result must be 2^E mod m, and the digits must
+equal the oracle's term floor((2^e mod m) 2^W / m) mod 2^W (Eq. 5).  The launch
+parameters (path, window, first window) come from the library's own planner
+(bbp_explain); the exponents include the warp-maximum padding the kernel uses
+and all-ones exponents that take the largest shift in every group.
+"""
+
+import importlib.util
+import os
+import random
+
+import pytest
+
+from conftest import ROOT
+from oracle import bbp_oracle as o1
+
+M32 = (1 << 32) - 1
+M64 = (1 << 64) - 1
+
+
+@pytest.fixture(scope="module")
+def bbp():
+    spec = importlib.util.spec_from_file_location("_bbp_build", os.path.join(ROOT, "paper_1008_3171_gb300", "_build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    mod.build()
+    import paper_1008_3171_gb300 as m
+
+    return m
+
+
+def neg_inverse32(m0):
+    x = m0
+    for _ in range(4):
+        x = (x * ((2 - m0 * x) & M32)) & M32
+    assert (x * m0) & M32 == 1
+    return (-x) & M32
+
+
+def r_mod_m_bitserial(m, rbits):
+    l = m.bit_length()
+    r, q = 1 << (l - 1), 0
+    for _ in range(l - 1, rbits):
+        r <<= 1
+        q <<= 1
+        assert r <= M64                      # r < m < 2^60 before doubling
+        if r >= m:
+            r -= m
+            q |= 1
+    assert q == (1 << rbits) // m and r == (1 << rbits) % m
+    return q, r
+
+
+def r_mod_m_advance(q, r, m_next, a, rbits):
+    aq = q * a
+    assert aq <= M64                         # formed in 64 bits
+    if aq > r + 4 * m_next:
+        return r_mod_m_bitserial(m_next, rbits)
+    r2 = r - aq
+    while r2 < 0:
+        r2 += m_next
+        q -= 1
+    assert q == (1 << rbits) // m_next and r2 == (1 << rbits) % m_next
+    return q, r2
+
+
+def sqr_shift_redc64(x, s, m, mp, small, do_shift):
+    x0, x1 = x & M32, x >> 32
+    assert x1 < 1 << 31                      # d1 = x1 << 1 in one word
+    d1 = x1 << 1
+    p00, p01 = x0 * x0, x0 * d1
+    if small:
+        assert x1 * x1 <= M32                # path 1 keeps only the low word of x1^2
+        s1 = (p00 >> 32) + (p01 & M32)
+        c = s1 >> 32
+        s1 &= M32
+        s2 = (p01 >> 32) + (x1 * x1) + c
+        s3 = s2 >> 32
+        s2 &= M32
+    else:
+        p11 = x1 * x1
+        s1 = (p00 >> 32) + (p01 & M32)
+        c = s1 >> 32
+        s1 &= M32
+        s2 = (p11 & M32) + (p01 >> 32) + c
+        c = s2 >> 32
+        s2 &= M32
+        s3 = (p11 >> 32) + c
+        assert s3 <= M32
+    s0 = p00 & M32
+    T = s0 | s1 << 32 | s2 << 64 | s3 << 96
+    assert T == x * x
+    if do_shift:
+        assert 0 <= s < 32
+        assert (T << s) >> 128 == 0          # funnel shifts keep four words
+        T <<= s
+    t0, t1, t2, t3 = T & M32, (T >> 32) & M32, (T >> 64) & M32, T >> 96
+    m0, m1 = m & M32, m >> 32
+    # step 1: word 0 vanishes
+    u = (t0 * mp) & M32
+    assert (t0 + u * m0) & M32 == 0
+    h = ((u * m0) >> 32) + (1 if t0 else 0)
+    assert h <= M32
+    a = (t1 | t2 << 32) + u * m1
+    t3 += a >> 64
+    a &= M64
+    a += h
+    t3 += a >> 64
+    a &= M64
+    assert t3 <= M32
+    t1, t2 = a & M32, a >> 32
+    assert (T + u * m) >> 32 == t1 | t2 << 32 | t3 << 64
+    # step 2: word 1 vanishes; the 64-bit multiply-add must not carry out
+    u = (t1 * mp) & M32
+    h = ((u * m0) >> 32) + (1 if t1 else 0)
+    assert h <= M32
+    a = (t2 | t3 << 32) + u * m1
+    assert a <= M64
+    a += h
+    assert a <= M64
+    assert a < 2 * m
+    return a
+
+
+def hensel_step64(x, m, mp):
+    x0, x1 = x & M32, x >> 32
+    q = (x0 * mp) & M32
+    h = ((q * (m & M32)) >> 32) + (1 if x0 else 0)
+    assert h <= M32
+    r = q * (m >> 32) + h + x1
+    assert r <= M64 and r == (x + q * m) >> 32 and (x + q * m) & M32 == 0
+    return q, r
+
+
+def sqr_shift_redc32(x, s, m, mp, do_shift):
+    T = x * x
+    if do_shift:
+        T <<= s
+    assert T <= M64
+    t0, t1 = T & M32, T >> 32
+    u = (t0 * mp) & M32
+    r = t1 + ((u * m) >> 32) + (1 if t0 else 0)
+    assert r <= M32 and r < 2 * m
+    return r
+
+
+def ladder_term(path, window, first, m, E, W, extra, r_mod_m):
+    """2^E mod m by the kernel's ladder, then the W-bit quotient digits."""
+    rb = 64 if path else 32
+    mp = neg_inverse32(m & M32)
+    v = E - rb
+    assert v >= 0
+    nb = v.bit_length() + extra              # the warp's longest exponent
+    h = min(first, nb - 1) if nb > 0 else 0
+    low = nb - h
+    w0 = (v >> low) if h > 0 else 0
+    x = r_mod_m << w0
+    assert x < 1 << rb
+    rem = v & ((1 << low) - 1) if low > 0 else 0
+    p = low
+    while p > 0:
+        ln = min(window, p)
+        p -= ln
+        for i in range(ln):
+            last = i == ln - 1
+            sh = ((rem >> p) & ((1 << ln) - 1)) if last else 0
+            if path:
+                x = sqr_shift_redc64(x, sh, m, mp, path == 1, last)
+            else:
+                x = sqr_shift_redc32(x, sh, m, mp, last)
+    assert x % m == pow(2, E, m)
+    if x >= m:
+        x -= m
+    digits = []
+    for _ in range(W // 32):
+        if path:
+            q, x = hensel_step64(x, m, mp)
+        else:
+            q = (x * mp) & M32
+            x = ((q * m) >> 32) + (1 if x else 0)
+        digits.append(q)
+    return sum(q << (32 * i) for i, q in enumerate(digits))
+
+
+CONFIGS = [
+    (0, 10**12, 256, 64, 30),
+    (0, 10**14 + 1, 256, 64, 30),
+    (0, 2 * 10**15 - 3, 256, 64, 30),
+    (0, 10**17 + 1, 64, 32, 30),
+    (1, 10**16 + 7, 1000, 64, 30),
+    (0, 10**7 + 1, 64, 64, 5),
+    (0, 10**9 + 1, 128, 64, 17),
+]
+
+
+@pytest.mark.parametrize("f,n,P,G,wide", CONFIGS)
+def test_word_model_matches_oracle_at_range_extremes(bbp, f, n, P, G, wide):
+    rng = random.Random(n ^ (P << 8) ^ wide)
+    F = o1.FORMULAS[f]
+    W = o1.working_bits(P, G)
+    d = n - 1
+    ranges, _ = bbp.bbp_explain(f, n, P, G, wide)
+    checked = 0
+    for r in ranges:
+        if r["tail"]:
+            continue
+        s = F.series[r["denominator"]]
+        path, window, first = r["path"], r["window"], r["first"]
+        rb = 64 if path else 32
+        k_last = r["k_begin"] + r["count"] - 1
+        ks = sorted({r["k_begin"], min(r["k_begin"] + 1, k_last), k_last}
+                    | {rng.randrange(r["k_begin"], k_last + 1) for _ in range(3)})
+        q = rr = None
+        prev = None
+        for k in ks:
+            m = s.a * k + s.b
+            if prev is not None and k == prev + 1:
+                q, rr = r_mod_m_advance(q, rr, m, s.a, rb)
+            else:
+                q, rr = r_mod_m_bitserial(m, rb)
+            prev = k
+            E = d + s.c - F.step * k + W
+            want = o1.term(F, s, d, k, W)
+            for extra in (0, 2):
+                assert ladder_term(path, window, first, m, E, W, extra, rr) % (1 << W) == want, (f, n, k, extra)
+            # the largest shifts: an all-ones exponent of the same length, at the range's largest modulus
+            m_max = s.a * k_last + s.b
+            E1 = rb + (1 << max(1, (E - rb).bit_length())) - 1
+            x = ladder_term(path, window, first, m_max, E1, 64, 0, (1 << rb) % m_max)
+            assert x == (-pow(2, E1, m_max) * pow(m_max, -1, 1 << 64)) % (1 << 64)
+            checked += 1
+    assert checked > 0
+
+
+def test_quotient_digits_are_the_exact_division():
+    """Fed s = x 2^W mod m, the digits q_i with s + (sum q_i 2^(32 i)) m = 0
+    mod 2^W are floor(x 2^W / m): the W-bit fraction of x / m without a
+    reciprocal (the ladder delivers s = 2^(e + W) mod m, i.e. x = 2^e mod m).
+    Checked against the definition for random odd moduli of every width."""
+    rng = random.Random(5)
+    for _ in range(300):
+        bits = rng.choice((5, 20, 29, 31, 40, 47, 52, 59))
+        m = rng.randrange(1 << (bits - 1), 1 << bits) | 1
+        x = rng.randrange(0, m)
+        W = 32 * rng.randrange(2, 12)
+        mp = neg_inverse32(m & M32)
+        y, digits = (x << W) % m, []
+        for _ in range(W // 32):
+            q, y = hensel_step64(y, m, mp)
+            digits.append(q)
+        t = sum(q << (32 * i) for i, q in enumerate(digits))
+        assert t == (x << W) // m
