@@ -268,3 +268,45 @@ def test_quotient_digits_are_the_exact_division():
             digits.append(q)
         t = sum(q << (32 * i) for i, q in enumerate(digits))
         assert t == (x << W) // m
+
+
+def tail_term_model(s, F, d, k, W):
+    """Tail term (e < 0) as the tail kernel forms it: q = floor(2^W / m) from the
+    exact-division digits of 2^W mod m (doubling, then Hensel steps), shifted
+    right by b = -e (Sec. 4.3: shift, then divide to W - b bits)."""
+    e = d + s.c - F.step * k
+    b = -e
+    m = s.a * k + s.b
+    assert 1 <= b
+    if b > W:
+        return 0
+    if m == 1:
+        return 1 << (W - b)
+    x = 1
+    for _ in range(W):                        # 2^W mod m by doubling; m < 2^62 keeps 2x in 64 bits
+        x <<= 1
+        assert x <= M64
+        if x >= m:
+            x -= m
+    mp = neg_inverse32(m & M32)
+    digits = []
+    for _ in range(W // 32):
+        q, x = hensel_step64(x, m, mp)
+        digits.append(q)
+    q = sum(v << (32 * i) for i, v in enumerate(digits))
+    assert q == (1 << W) // m % (1 << W)
+    return q >> b
+
+
+@pytest.mark.parametrize("f,n,P,G,wide", CONFIGS + [(0, 1, 64, 32, 30), (1, 2, 8, 32, 30), (0, 9, 8, 64, 30)])
+def test_tail_model_matches_oracle(bbp, f, n, P, G, wide):
+    F = o1.FORMULAS[f]
+    W = o1.working_bits(P, G)
+    d = n - 1
+    ranges, _ = bbp.bbp_explain(f, n, P, G, wide)
+    tails = [r for r in ranges if r["tail"]]
+    assert tails
+    for r in tails:
+        s = F.series[r["denominator"]]
+        for k in range(r["k_begin"], r["k_begin"] + r["count"]):
+            assert tail_term_model(s, F, d, k, W) == o1.term(F, s, d, k, W), (f, n, k)
