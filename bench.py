@@ -119,8 +119,12 @@ class ClockSampler:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                  "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
-        except (OSError, FileNotFoundError):
+        except (OSError, FileNotFoundError):   # no nvidia-smi: the run reports no clocks
             self.proc = None
+            if getattr(self, "fh", None):
+                self.fh.close()
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
 
     def stop(self):
         if not self.proc:

@@ -77,3 +77,33 @@ def test_reference_arm_is_silent_on_other_ranks(rank):
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
                         "--warmup", "3"], capture_output=True, text=True, timeout=120, cwd=ROOT, env=env)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_clock_sampler_start_stop_with_a_fake_nvidia_smi(tmp_path, monkeypatch):
+    """The sampler's whole start/stop path against a stand-in nvidia-smi that
+    prints samples every 50 ms until it is terminated."""
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\n"
+                    "while true; do\n"
+                    "  echo '0, 2070, 2070, 1100.00, 0x0000000000000004, Not Active, Not Active, Not Active, Active'\n"
+                    "  sleep 0.05\n"
+                    "done\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}{os.pathsep}{os.environ['PATH']}")
+    import time
+
+    s = bench.ClockSampler(0)
+    s.start()
+    time.sleep(0.4)
+    got = s.stop()
+    assert got is not None and got["sm_mhz"] == 2070.0 and got["sm_max_mhz"] == 2070.0
+    assert got["reasons"] == ["sw_power_cap"] and got["samples"] >= 2
+    assert not os.path.exists(s.path)
+
+
+def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
+    monkeypatch.setenv("PATH", str(tmp_path))
+    s = bench.ClockSampler(0)
+    s.start()
+    assert s.stop() is None
+    assert not os.path.exists(s.path)               # its sample file is gone too
