@@ -160,6 +160,13 @@ def bbp_status_str(status: int) -> str:
     return _lib.bbp_status_str(status).decode()
 
 
+def bbp_plan_opts_default() -> dict:
+    """The library's default plan options (host-only; no GPU)."""
+    opts = bbp_plan_opts()
+    _lib.bbp_plan_opts_default(ctypes.byref(opts))
+    return {f: getattr(opts, f) for f, _ in bbp_plan_opts._fields_}
+
+
 def bbp_plan_create(device: int = 0, stream: Optional[int] = None, guard_bits: int = 64,
                     accum_mem_budget: int = 0, max_slots: int = 0, tune_table: Optional[str] = None,
                     profile: bool = False, strict: bool = False) -> int:

@@ -43,9 +43,9 @@ def test_binding_exposes_abi_names(lib):
     import paper_1008_3171_gb300 as bbp
 
     for name in declared_functions():
-        if name in ("bbp_plan_opts_default",):
-            continue
         assert hasattr(bbp, name), name
+    d = bbp.bbp_plan_opts_default()
+    assert d["guard_bits"] == 64 and d["device"] == 0 and d["tune_table"] is None and d["strict"] == 0
 
 
 def test_host_helpers(lib):
