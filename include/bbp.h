@@ -199,7 +199,11 @@ bbp_status bbp_finalize_async(bbp_plan p, bbp_formula f, uint64_t n, uint32_t P,
  * bytes, out_stride >= ceil(max P / 8); query q's bits at out + q * out_stride,
  * MSB first.  valid_bits[count] (may be NULL): certified bits.  latency_ms[count]
  * (may be NULL): device time from the start of the pass to each query's finalize.
- * Blocks until done.  EINVAL: a bad query or a too-small out_stride. */
+ * Blocks until done.  EINVAL: a bad query or a too-small out_stride.  ERANGE: a
+ * modulus would reach 2^60, or a query needs 2^32 - 2^24 or more warp tiles (more
+ * than about 8.8e12 head terms at the default 2048-term tile, n above about
+ * 1.2e13), past which its 64-bit carry-save limbs could overflow; run such a
+ * query with bbp_bits or bbp_accumulate_async. */
 bbp_status bbp_bits_batch(bbp_plan p, bbp_formula f, uint32_t count, const uint64_t* n, const uint32_t* P,
                           uint8_t* out, uint32_t out_stride, uint32_t* valid_bits, double* latency_ms);
 
@@ -217,7 +221,8 @@ bbp_status bbp_bits_batch(bbp_plan p, bbp_formula f, uint32_t count, const uint6
 typedef uint64_t bbp_ticket;
 
 /* Queues the query (bits n .. n+P-1 by Eq. 2).  BBP_EBUSY: the wait queue is as
- * long as the slot pool; retry later.  EINVAL/ERANGE as bbp_bits. */
+ * long as the slot pool; retry later.  EINVAL/ERANGE as bbp_bits, and ERANGE for
+ * a query too large for the queue kernels' carry-save limbs (as bbp_bits_batch). */
 bbp_status bbp_submit(bbp_plan p, uint64_t n, uint32_t P, bbp_ticket* t);
 
 /* BBP_PENDING while the query runs; BBP_OK once done, then out (ceil(P/8) host

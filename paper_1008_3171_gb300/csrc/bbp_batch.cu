@@ -174,6 +174,10 @@ static bbp_status plan_batch(bbp_plan p, int f, uint32_t count, const uint64_t* 
       if (st != 0) return BBP_EINVAL;
       N += natural_end(F, j, n[q] - 1, W);
     }
+    uint64_t qtiles = 0;
+    for (const TermRange& r : ranges)
+      if (!r.tail) qtiles += (r.count + tile - 1) / tile;
+    if (qtiles > kMaxQueueTiles) return BBP_ERANGE;  // carry-save limbs could pass 2^64
     for (const TermRange& r : ranges) {
       const SeriesDef& s = F.s[r.j];
       qterms[q] += r.count;

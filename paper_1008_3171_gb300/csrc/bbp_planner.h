@@ -31,6 +31,10 @@ constexpr int kWideMinBits = 30;             // moduli with bitlen >= 30 take a 
 constexpr int kWideFloorBits = 5;
 constexpr int kSmallMaxBits = 47;            // 64-bit path 1 (x1^2 < 2^32) up to this bitlen
 constexpr int kMaxModulusBits = 60;          // 64-bit path bound
+// The persistent queue kernels add one 32-bit partial sum per hand-out (at least
+// one warp tile) to a query's 64-bit carry-save limbs; a query of fewer than this
+// many head tiles (plus its few tail terms) keeps every limb's sum below 2^64.
+constexpr uint64_t kMaxQueueTiles = (1ull << 32) - (1ull << 24);
 
 // A contiguous run of terms of one series with one kernel configuration.
 struct TermRange {

@@ -223,6 +223,10 @@ bbp_status plan_query_work(bbp_plan p, uint64_t n, uint32_t P, Query* q) {
     }
     q->work.push_back(w);
   }
+  uint64_t tiles = 0;
+  for (const Work& w : q->work)
+    if (!w.tail) tiles += w.tiles;
+  if (tiles > kMaxQueueTiles) return BBP_ERANGE;  // carry-save limbs could pass 2^64
   if (q->work.empty()) {  // nothing to sum: a zero-length tail still retires the query
     Work w{};
     w.tail = true;

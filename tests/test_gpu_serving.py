@@ -99,3 +99,28 @@ def test_tickets(bbp):
             bbp.bbp_submit(plan.handle, 0, 8)
     finally:
         plan.close()
+
+
+def test_query_too_large_for_the_queue_limbs_is_refused(bbp, tmp_path):
+    """A query needing 2^32 - 2^24 or more warp tiles could overflow its 64-bit
+    carry-save limbs in the queue kernels: bbp_submit and bbp_bits_batch refuse it
+    with BBP_ERANGE while planning, before any launch.  With run = 2 a tile is 64
+    terms, so n = 5e11 (3.5e11 head terms, 5.5e9 tiles) is past the limit and
+    n = 1e11 (1.1e9 tiles) is not."""
+    import json
+
+    table = tmp_path / "tune.json"
+    table.write_text(json.dumps({"run": 2}))
+    plan = bbp.Plan(device=0, guard_bits=64, tune_table=str(table))
+    try:
+        with pytest.raises(bbp.BBPError) as e:
+            bbp.bbp_submit(plan.handle, 5 * 10**11, 64)
+        assert e.value.status == bbp.BBP_ERANGE
+        with pytest.raises(bbp.BBPError) as e:
+            bbp.bbp_bits_batch(plan.handle, 0, [1000, 5 * 10**11], [64, 64])
+        assert e.value.status == bbp.BBP_ERANGE
+        t = bbp.bbp_submit(plan.handle, 10**6, 64)      # a small query is still served
+        assert t is not None
+        assert wait_all(bbp, plan, {t: (10**6, 64)})[t] == oracle.c_bits(10**6, 64, 64)
+    finally:
+        plan.close()
