@@ -61,7 +61,7 @@ typedef struct bbp_plan_opts {
   void* stream;             /* cudaStream_t for all work; NULL: the plan creates its own */
   uint32_t guard_bits;      /* G: positive multiple of 32; 0 selects 64 */
   size_t accum_mem_budget;  /* bytes of device accumulator memory for queued queries; 0: 64 MiB */
-  uint32_t max_slots;       /* concurrent queries admitted by bbp_submit; 0: 4096 */
+  uint32_t max_slots;       /* concurrent queries admitted by bbp_submit; 0: 4096; at most 2^24 are used */
   const char* tune_table;   /* path of an autotune table or NULL for defaults.  JSON object; keys (others
                                ignored, out-of-range values keep the default): run (even, 2..4096, terms
                                per stream; 64), streams (1 or 2; 1), cta (head-kernel threads per CTA,
@@ -199,7 +199,7 @@ bbp_status bbp_finalize_async(bbp_plan p, bbp_formula f, uint64_t n, uint32_t P,
  * bytes, out_stride >= ceil(max P / 8); query q's bits at out + q * out_stride,
  * MSB first.  valid_bits[count] (may be NULL): certified bits.  latency_ms[count]
  * (may be NULL): device time from the start of the pass to each query's finalize.
- * Blocks until done.  EINVAL: a bad query or a too-small out_stride.  ERANGE: a
+ * Blocks until done.  EINVAL: a bad query, a too-small out_stride or count > 2^24.  ERANGE: a
  * modulus would reach 2^60, or a query needs 2^32 - 2^24 or more warp tiles (more
  * than about 8.8e12 head terms at the default 2048-term tile, n above about
  * 1.2e13), past which its 64-bit carry-save limbs could overflow; run such a

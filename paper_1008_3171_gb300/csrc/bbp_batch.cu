@@ -315,6 +315,7 @@ extern "C" bbp_status bbp_bits_batch(bbp_plan p, bbp_formula f, uint32_t count, 
                                      uint8_t* out, uint32_t out_stride, uint32_t* valid_bits, double* latency_ms) {
   if (!p || (f != BBP_BELLARD && f != BBP_BBP) || (count && (!n || !P || !out))) return BBP_EINVAL;
   if (count == 0) return BBP_OK;
+  if (count > kMaxQueueQueries) return BBP_EINVAL;
   uint32_t maxbytes = 0;
   for (uint32_t q = 0; q < count; ++q) maxbytes = std::max(maxbytes, (P[q] + 7) / 8);
   if (out_stride < maxbytes) return BBP_EINVAL;

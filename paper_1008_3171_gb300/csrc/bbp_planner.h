@@ -35,6 +35,9 @@ constexpr int kMaxModulusBits = 60;          // 64-bit path bound
 // one warp tile) to a query's 64-bit carry-save limbs; a query of fewer than this
 // many head tiles (plus its few tail terms) keeps every limb's sum below 2^64.
 constexpr uint64_t kMaxQueueTiles = (1ull << 32) - (1ull << 24);
+// Queries of one batched pass, and serving slots: 2^24 keeps every query's 32-bit
+// output byte offset (query index x 160 bytes) below 2^32.
+constexpr uint32_t kMaxQueueQueries = 1u << 24;
 
 // A contiguous run of terms of one series with one kernel configuration.
 struct TermRange {

@@ -543,7 +543,8 @@ ServeEngine* engine_of(bbp_plan p, bbp_status* st) {
   }
   E->plan = p;
   const size_t per_slot = sizeof(unsigned long long) * kMaxLimbs + kOutStride + 64;
-  E->max_slots = static_cast<uint32_t>(std::max<size_t>(1, std::min<size_t>(p->max_slots, p->accum_budget / per_slot)));
+  E->max_slots = static_cast<uint32_t>(
+      std::max<size_t>(1, std::min<size_t>({p->max_slots, p->accum_budget / per_slot, kMaxQueueQueries})));
   cudaSetDevice(p->device);
   if (!alloc_engine(E)) {
     free_engine(E);
