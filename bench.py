@@ -39,6 +39,9 @@ METRIC = "BBP terms/s at n=1e12 P=256; % of INT32 IMAD peak; batched p50/p99 lat
 WORKLOAD = "plain single query: Bellard formula, n=1e12, P=256 + 64 guard bits, all 7 series"
 IMAD_LANES_PER_CLK_PER_SM = 64     # 32-bit multiply-add (low half) issue rate per SM, measured by bbp_imad_probe
 SM_MAX_MHZ_FALLBACK = 2070.0       # GB300 maximum SM clock
+# Eq. 2: the exponent of series j's term k is n - 1 + c_j - 10 k
+BELLARD_STEP = 10
+BELLARD_EXP_OFFSETS = (2, 0, -4, -4, -6, -1, -6)
 
 
 def parse_args():
@@ -57,6 +60,8 @@ def parse_args():
     ap.add_argument("--tune-table", default=None)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target wall time of one oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched persistent-vs-plain comparison that follows the single-query steps")
     return ap.parse_args()
 
 
@@ -97,6 +102,35 @@ def oracle_sample(n: int, P: int, G: int, target_s: float, threads: int = 0):
 
 def host_cores() -> int:
     return os.cpu_count() or 1
+
+
+def survey_imad_model(bbp, n: int, P: int, G: int) -> float:
+    """Multiply instructions of the query's head terms by the survey's per-term model:
+    16 ceil(log2 e) + 4 L + 50 for a two-limb (64-bit) modulus, 5 ceil(log2 e) + 3 L + 25
+    for a one-limb modulus (below 2^31), L = W/32 limbs, e the term's exponent; summed
+    exactly over the query's exponents (counted per bit length), host-only."""
+    ranges, _ = bbp.bbp_explain(0, n, P, G)
+    L = ((P + 31) // 32 * 32 + G) // 32
+    step, cs = BELLARD_STEP, BELLARD_EXP_OFFSETS
+    d = n - 1
+    total = 0
+    for r in ranges:
+        if r["tail"]:
+            continue
+        c = cs[r["denominator"]]
+        k_lo, k_hi = r["k_begin"], r["k_begin"] + r["count"] - 1
+        one_limb = r["path"] in (0, 3)
+        # e = d + c - step k; count terms per ceil(log2 e) = b, i.e. 2^(b-1) < e <= 2^b (b = 0: e <= 1)
+        for b in range(0, 64):
+            e_lo = 0 if b == 0 else (1 << (b - 1)) + 1
+            e_hi = 1 if b == 0 else 1 << b
+            # k with e_lo <= d + c - step k <= e_hi
+            ka = max(k_lo, -((e_hi - d - c) // step))
+            kb = min(k_hi, (d + c - e_lo) // step)
+            if kb >= ka:
+                per = (5 * b + 3 * L + 25) if one_limb else (16 * b + 4 * L + 50)
+                total += (kb - ka + 1) * per
+    return float(total)
 
 
 # ---------------------------------------------------------------- clocks
@@ -167,6 +201,19 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(loaded) if loaded else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- streams
+
+def work_stream(torch, dev):
+    """A created CUDA stream, made torch's current stream, for every library call and
+    every event of a run.  The legacy default stream will not do: its handle is 0,
+    which the library reads as "the plan's own stream", so events recorded on it
+    would not be ordered with the library's work."""
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    assert stream.cuda_stream != 0
+    return stream
 
 
 # ---------------------------------------------------------------- distributed
@@ -257,7 +304,7 @@ def run_gpu(args):
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=dev)
-    stream = torch.cuda.current_stream()
+    stream = work_stream(torch, dev)
     plan = bbp.Plan(device=local, stream=stream.cuda_stream, guard_bits=GUARD, profile=True)
     W = plan.working_bits(P_BITS)
     L = W // 32
@@ -353,9 +400,28 @@ def run_gpu(args):
     max_mhz = (clocks or {}).get("sm_max_mhz") or SM_MAX_MHZ_FALLBACK
     peak = sms * IMAD_LANES_PER_CLK_PER_SM * max_mhz * 1e6 / 1e12        # T multiply instructions / s
     achieved = (imad / (head_ms / 1e3)) / 1e12 if head_ms > 0 else None
+    survey = survey_imad_model(bbp, N_POS, P_BITS, GUARD) * args.steps / max(1, world)
+    achieved_survey = (survey / (head_ms / 1e3)) / 1e12 if head_ms > 0 else None
     value = terms / t_dev
     e2e_value = terms / t_e2e
     ncu = head_kernel_ncu()
+
+    batched = None
+    if not args.no_batched and world == 1:
+        import workloads
+
+        ns, Ps = workloads.batched_queries(count=args.batch_count, seed=0)
+        wn, wP = workloads.batched_queries(count=64, seed=99, lo=3.0, hi=8.0)
+        bplan = bbp.Plan(device=local, stream=stream.cuda_stream, guard_bits=GUARD)   # no per-launch events
+        try:
+            bbp.bbp_bits_batch(bplan.handle, 0, wn, wP, with_latency=False)        # warm-up: graph, buffers
+            pers, plain, identical, bterms, certified = batched_arms(bbp, bplan, stream, ns, Ps)
+        finally:
+            bplan.close()
+        batched = {"workload": f"{len(ns)} queries, seed 0, n = floor(10^U(4,10)), P uniform in {{64,128,256}}, "
+                               f"G = {GUARD}", "terms": bterms, "persistent": pers, "plain": plain,
+                   "latency": "device time from the start of the arm to each query's finalize (both arms)",
+                   "identical": identical, "all_certified": certified}
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -373,20 +439,87 @@ def run_gpu(args):
                 "d2h_bytes_per_step": nbytes + 4,
                 "note": "bbp_bits with host output; the query (n, P) travels as kernel arguments"},
         "gpu_launches": launches,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T IMAD/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": ncu.get("dram_bytes_per_launch"),
+        "roofline": {"bound": "alu", "achieved": achieved_survey, "peak": peak, "unit": "T IMAD/s",
+                     "frac": (achieved_survey / peak) if achieved_survey else None,
+                     "traffic": ncu.get("dram_bytes_per_launch"),
+                     "model": "survey: 16 ceil(log2 e) + 4L + 50 IMAD per two-limb term, 5 ceil(log2 e) + 3L + 25 "
+                              "per one-limb term, summed over the query's exponents",
+                     "achieved_half_products": achieved,
+                     "frac_half_products": (achieved / peak) if achieved else None,
+                     "half_products_model": "32-bit product halves the method needs: 13 per two-limb squaring "
+                                            "(14 when x1^2 needs its high word), 4 per one-limb squaring, 4 (2) per "
+                                            "quotient digit, 6 for m^-1 mod 2^32",
                      "ncu_imad_pipe_frac": ncu.get("fma_pipe_frac_of_imad_rate"),
                      "kernel": "head_kernel", "head_launches": head_launches,
-                     "peak_basis": f"{sms} SMs x {IMAD_LANES_PER_CLK_PER_SM} IMAD lanes/clk x {max_mhz:.0f} MHz"},
+                     "peak_basis": f"{sms} SMs x {IMAD_LANES_PER_CLK_PER_SM} IMAD lanes/clk (mul.lo issue rate, "
+                                   f"measured) x {max_mhz:.0f} MHz; achieved = modelled multiplies of the "
+                                   "head terms / summed CUDA-event time of the head launches"},
         "cpu_baseline": cpu,
         "clocks": clocks,
         "verified": verified,
+        "batched": batched,
     })
     if world > 1:
         dist.destroy_process_group()
 
 
 # ---------------------------------------------------------------- batched workload
+
+def batched_arms(bbp, plan, stream, ns, Ps):
+    """One persistent graph-captured pass (bbp_bits_batch) and the plain form (one
+    bbp_bits_async per query, back to back on the same stream) over the same
+    queries.  Latency in both arms is device time from the arm's start to each
+    query's finalize: the pass's global-timer stamps for the persistent form, a CUDA
+    event after each query for the plain form.  Returns (persistent, plain, identical,
+    terms, all certified); a query whose two results differ is listed in persistent["differs"]."""
+    import torch
+
+    count = len(ns)
+    stride = max((int(P) + 7) // 8 for P in Ps)
+    # persistent
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    vals, valid, lat = bbp.bbp_bits_batch(plan.handle, 0, ns, Ps)
+    e1.record(stream)
+    e1.synchronize()
+    pers_s = e0.elapsed_time(e1) / 1e3
+    terms = plan.stats()["terms"]
+    # plain
+    d_out = torch.zeros((count, stride), dtype=torch.uint8, device="cuda")
+    d_valid = torch.zeros(count, dtype=torch.int32, device="cuda")
+    start = torch.cuda.Event(enable_timing=True)
+    evs = []
+    torch.cuda.synchronize()
+    start.record(stream)
+    for q, (n, P) in enumerate(zip(ns, Ps)):
+        bbp.bbp_bits_async(plan.handle, 0, int(n), int(P), d_out[q].data_ptr(), d_valid[q].data_ptr(), 0,
+                           stream.cuda_stream)
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        evs.append(e)
+    evs[-1].synchronize()
+    plain_lat = [start.elapsed_time(e) for e in evs]
+    plain_s = plain_lat[-1] / 1e3
+    out = d_out.cpu().tolist()
+    vv = d_valid.cpu().tolist()
+    plain_vals = []
+    for q, P in enumerate(Ps):
+        nb = (int(P) + 7) // 8
+        plain_vals.append(int.from_bytes(bytes(out[q][:nb]), "big") >> (8 * nb - int(P)))
+    diff = [q for q in range(count) if (plain_vals[q], vv[q]) != (vals[q], valid[q])]
+    identical = not diff
+    persistent = {"terms_per_s": terms / pers_s, "device_s": pers_s, "p50_ms": percentile(lat, 50),
+                  "p99_ms": percentile(lat, 99)}
+    plain = {"terms_per_s": terms / plain_s, "device_s": plain_s, "p50_ms": percentile(plain_lat, 50),
+             "p99_ms": percentile(plain_lat, 99)}
+    if diff:   # which queries, with both forms' bits (hex) and certified counts
+        persistent["differs"] = [{"q": q, "n": int(ns[q]), "P": int(Ps[q]), "persistent": [hex(vals[q]), valid[q]],
+                                  "plain": [hex(plain_vals[q]), vv[q]]} for q in diff[:8]]
+        persistent["differs_count"] = len(diff)
+    return persistent, plain, identical, terms, all(v == P for v, P in zip(valid, Ps))
+
 
 def percentile(values, q):
     v = sorted(values)
@@ -399,51 +532,31 @@ def percentile(values, q):
 def run_batched(args):
     """4096 seeded queries (n log-uniform in [1e4, 1e10], P in {64, 128, 256}, G = 64):
     one persistent graph-captured pass (bbp_bits_batch) against the plain form (one
-    bbp_bits call per query, in submission order); outputs must be identical."""
+    query after another on the same stream); outputs must be identical.  Latency in
+    both arms is device time from the arm's start to each query's finalize."""
     import torch
 
     import paper_1008_3171_gb300 as bbp
     import workloads
 
     ns, Ps = workloads.batched_queries(count=args.batch_count, seed=0)
-    plan = bbp.Plan(device=0, guard_bits=GUARD, tune_table=args.tune_table)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = work_stream(torch, torch.device("cuda", 0))
+    plan = bbp.Plan(device=0, stream=stream.cuda_stream, guard_bits=GUARD, tune_table=args.tune_table)
     for _ in range(args.warmup):
-        bbp.bbp_bits_batch(plan.handle, 0, ns, Ps, with_latency=False)
+        wn, wP = workloads.batched_queries(count=64, seed=99, lo=3.0, hi=8.0)
+        bbp.bbp_bits_batch(plan.handle, 0, wn, wP, with_latency=False)
     sampler = ClockSampler(0)
     sampler.start()
-    per = []
-    for _ in range(args.steps):
-        flush.fill_(1)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        vals, valid, lat = bbp.bbp_bits_batch(plan.handle, 0, ns, Ps)
-        per.append(time.perf_counter() - t0)
-    batch_stats = plan.stats()
-    terms = batch_stats["terms"]
-    flush.fill_(2)
-    torch.cuda.synchronize()
-    plain_lat = []
-    plain_vals = []
-    t0 = time.perf_counter()
-    for n, P in zip(ns, Ps):
-        v, ok = plan.bits(n, P)
-        plain_vals.append((v, ok))
-        plain_lat.append(1e3 * (time.perf_counter() - t0))
-    plain_s = time.perf_counter() - t0
+    runs = [batched_arms(bbp, plan, stream, ns, Ps) for _ in range(args.steps)]
     clocks = sampler.stop()
-    identical = plain_vals == list(zip(vals, valid))
-    t = sum(per) / len(per)
+    pers, plain, identical, terms, certified = runs[-1]
     emit({
         "metric": "batched: terms/s and p50/p99 query latency, persistent vs plain", "workload": "batched",
         "config": {"queries": len(ns), "seed": 0, "n": "floor(10^U(4,10))", "P": "uniform {64,128,256}",
                    "guard_bits": GUARD, "terms": terms, "tune_table": args.tune_table},
-        "persistent": {"terms_per_s": terms / t, "wall_s": t, "p50_ms": percentile(lat, 50),
-                       "p99_ms": percentile(lat, 99), "latency": "device time from pass start to each finalize",
-                       "launches": batch_stats["kernel_launches"], "steps": args.steps, "warmup": args.warmup},
-        "plain": {"terms_per_s": terms / plain_s, "wall_s": plain_s, "p50_ms": percentile(plain_lat, 50),
-                  "p99_ms": percentile(plain_lat, 99), "latency": "host time from start to each bbp_bits return"},
-        "identical": identical, "all_certified": all(ok == P for (v, ok), P in zip(plain_vals, Ps)),
+        "persistent": dict(pers, steps=args.steps, warmup=args.warmup), "plain": plain,
+        "latency": "device time from the start of the arm to each query's finalize (both arms)",
+        "identical": all(r[2] for r in runs), "all_certified": certified,
         "clocks": clocks,
     })
 

@@ -247,7 +247,7 @@ def bbp_shard_range(formula: int, denominator: int, n: int, W: int, shard: int, 
     return kb.value, ke.value
 
 
-def bbp_explain(formula: int, n: int, P: int, guard_bits: int = 64, wide_min_bits: int = 30) -> tuple[list, int]:
+def bbp_explain(formula: int, n: int, P: int, guard_bits: int = 64, wide_min_bits: int = 32) -> tuple[list, int]:
     """Host-only launch plan of a query: (ranges as dicts, terms covered).  No GPU."""
     count = ctypes.c_uint32()
     terms = ctypes.c_uint64()

@@ -19,7 +19,9 @@ LIB = os.path.join(HERE, "libbbp.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), "-I", CSRC]
-SOURCES = ["bbp_kernels.cu", "bbp_runtime.cu", "bbp_planner.cpp", "bbp_tune.cpp", "bbp_noalloc.cu", "bbp_batch.cu", "bbp_serve.cu"]
+SOURCES = ["bbp_kernels.cu", "bbp_lmax3.cu", "bbp_lmax4.cu", "bbp_lmax6.cu", "bbp_lmax10.cu", "bbp_lmax16.cu", "bbp_lmax24.cu",
+           "bbp_lmax40.cu", "bbp_runtime.cu", "bbp_planner.cpp", "bbp_tune.cpp", "bbp_noalloc.cu", "bbp_batch.cu",
+           "bbp_serve.cu"]
 
 
 def nvcc() -> str:

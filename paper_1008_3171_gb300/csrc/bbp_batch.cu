@@ -149,7 +149,6 @@ struct BatchPlan {
 static bbp_status plan_batch(bbp_plan p, int f, uint32_t count, const uint64_t* n, const uint32_t* P,
                              BatchState* b, BatchPlan* bp) {
   const FormulaDef& F = formula_def(f);
-  const uint64_t tile = 32ull * p->streams * p->run;
   std::vector<std::vector<HeadArgs>> vj(kVariants);
   std::vector<std::vector<uint32_t>> vq(kVariants);
   std::vector<std::vector<uint64_t>> vt(kVariants);
@@ -176,7 +175,7 @@ static bbp_status plan_batch(bbp_plan p, int f, uint32_t count, const uint64_t* 
     }
     uint64_t qtiles = 0;
     for (const TermRange& r : ranges)
-      if (!r.tail) qtiles += (r.count + tile - 1) / tile;
+      if (!r.tail) qtiles += (r.count + tile_terms(p, r.path) - 1) / tile_terms(p, r.path);
     if (qtiles > kMaxQueueTiles) return BBP_ERANGE;  // carry-save limbs could pass 2^64
     for (const TermRange& r : ranges) {
       const SeriesDef& s = F.s[r.j];
@@ -215,10 +214,10 @@ static bbp_status plan_batch(bbp_plan p, int f, uint32_t count, const uint64_t* 
         a.window = r.window;
         a.first = r.first;
         a.slots = slots;
-        const int v = lmax_index(lmax) * 3 + r.path;
+        const int v = lmax_index(lmax) * kNumPaths + r.path;
         vj[v].push_back(a);
         vq[v].push_back(q);
-        vt[v].push_back((r.count + tile - 1) / tile);
+        vt[v].push_back((r.count + tile_terms(p, r.path) - 1) / tile_terms(p, r.path));
         bp->head_terms += r.count;
         bp->imad += r.imad;
       }
@@ -392,9 +391,9 @@ extern "C" bbp_status bbp_bits_batch(bbp_plan p, bbp_formula f, uint32_t count, 
     for (int v = 0; v < kVariants; ++v) {
       const uint32_t jb = bp.group_begin[w * kVariants + v], je = bp.group_begin[w * kVariants + v + 1];
       if (jb == je) continue;
-      const int lmax = kLmaxClasses[v / 3], path = v % 3;
-      const int blocks = queue_occupancy(path, p->streams, lmax) * p->sm_count;
-      chk(launch_queue(dev, jb, je, cur + v, path, p->streams, lmax, blocks, s));
+      const int lmax = kLmaxClasses[v / kNumPaths], path = v % kNumPaths;
+      const int blocks = queue_occupancy(path, head_streams(p, path), lmax) * p->sm_count;
+      chk(launch_queue(dev, jb, je, cur + v, path, head_streams(p, path), lmax, blocks, s));
       ++launches;
       ++head_launches;
     }

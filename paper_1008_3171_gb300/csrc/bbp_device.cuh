@@ -30,11 +30,12 @@ __device__ __forceinline__ uint64_t make64(uint32_t lo, uint32_t hi) {
 }
 __device__ __forceinline__ int bitlen64(uint64_t v) { return 64 - __clzll(static_cast<long long>(v)); }
 
-// -m^-1 mod 2^32 for odd m.  An odd m is its own inverse mod 8 (m*m = 1 mod 8);
-// each step x <- x (2 - m x) doubles the number of correct low bits: 3,6,12,24,48.
+// -m^-1 mod 2^32 for odd m by Newton-Hensel lifting: each step x <- x (2 - m x)
+// doubles the number of correct low bits.  The start x = (3 m) XOR 2 is already
+// correct to 5 bits for every odd m (a known starting value; the word-level test
+// checks it on every odd residue mod 2^16), so three steps give 5, 10, 20, 40 >= 32.
 __device__ __forceinline__ uint32_t neg_inverse32(uint32_t m0) {
-  uint32_t x = m0;
-  x *= 2u - m0 * x;
+  uint32_t x = (3u * m0) ^ 2u;
   x *= 2u - m0 * x;
   x *= 2u - m0 * x;
   x *= 2u - m0 * x;
@@ -85,9 +86,8 @@ __device__ __forceinline__ void r_mod_m_advance(RTrack& t, uint64_t m_next, uint
 
 // ---------------------------------------------------------------- 64-bit Montgomery
 //
-// m = (m1:m0) odd, 2^31 <= m < 2^60, R = 2^64, mp = -m^-1 mod 2^32.
-// Invariant: x < 2m.  sqr_shift_redc returns REDC(x^2 * 2^s) < 2m, valid while
-// 2m^2 2^s 4 / R <= m, i.e. bitlen(m) + s <= 61.
+// m = (m1:m0) odd, 2^29 <= m < 2^60, R = 2^64, mp = -m^-1 mod 2^32.  Residues are
+// lazy: x < 2m.  A squaring with a window shift s returns REDC(x^2 2^s) < 2m.
 struct Mod64 {
   uint32_t m0, m1, mp;
 };
@@ -98,64 +98,44 @@ struct Mod64 {
 // without changing the result.
 //
 // Multiply mix.  On GB300 the integer multiply pipe issues the low half of a
-// 32x32 product (mul.lo / mad.lo) at 64 lanes/clk/SM, the high half (mul.hi) at 30
-// and the full 64-bit product (mul.wide) at 25.  So a product whose two halves are
-// both needed is one mul.wide, a product of which only the high half is needed is
-// one mul.hi, and the low word of T + u m -- zero by the choice of u -- is never
-// formed: its carry is (T_0 != 0), taken on the ALU.
-//
-// SMALL: x1^2 < 2^32 (bitlen(m) <= 47, since x < 2m), so x1^2 needs no high half.
-template <bool SMALL>
+// 32x32 product (mul.lo) at 64 lanes/clk/SM, the high half (mul.hi) and the full
+// product (mul.wide) at 32, and a full product with a 64-bit addend (mad.wide) at
+// only 25.  So a product whose two halves are both needed is one mul.wide without
+// an addend, a product of which only the high half is needed is one mul.hi, sums
+// are 32-bit carry chains on the ALU, and the low word of T + u m -- zero by the
+// choice of u -- is never formed: its carry is (T_0 != 0), produced as the carry
+// out of T_0 + (2^32 - 1) and consumed by the next add of the chain.
+
+// General squaring: x < 2^61 (so 2 x1 fits one word), T = x^2 2^s on four words,
+// then two word-by-word REDC steps T <- (T + u m) / 2^32.  The result is below 2m
+// when T < m 2^64: bitlen(m) + s <= 61 for a lazy x < 2m, and bitlen(m) + 2 w + s
+// <= 64 for the unreduced first window x < m 2^w.
 __device__ __forceinline__ void sqr_shift_redc64(uint32_t& x0, uint32_t& x1, uint32_t s, const Mod64& M,
                                                  bool do_shift) {
   uint32_t t0, t1, t2, t3;
-  // T = x0^2 + (x0 * 2 x1) 2^32 + x1^2 2^64, with 2 x1 < 2^32 because x < 2^61
-  if (SMALL) {
-    asm("{\n\t"
-        ".reg .u32 a0, a1, d1, s0, s1, s2, s3, q0, w0, w1;\n\t"
-        ".reg .u64 p00, p01;\n\t"
-        "mov.u32        a0, %4;\n\t"
-        "mov.u32        a1, %5;\n\t"
-        "shl.b32        d1, a1, 1;\n\t"
-        "mul.wide.u32   p00, a0, a0;\n\t"
-        "mul.wide.u32   p01, a0, d1;\n\t"
-        "mul.lo.u32     q0, a1, a1;\n\t"
-        "mov.b64        {s0, s1}, p00;\n\t"
-        "mov.b64        {w0, w1}, p01;\n\t"
-        "add.cc.u32     s1, s1, w0;\n\t"
-        "addc.cc.u32    s2, w1, q0;\n\t"
-        "addc.u32       s3, 0, 0;\n\t"
-        "mov.u32        %0, s0;\n\t"
-        "mov.u32        %1, s1;\n\t"
-        "mov.u32        %2, s2;\n\t"
-        "mov.u32        %3, s3;\n\t"
-        "}"
-        : "=r"(t0), "=r"(t1), "=r"(t2), "=r"(t3)
-        : "r"(x0), "r"(x1));
-  } else {
-    asm("{\n\t"
-        ".reg .u32 a0, a1, d1, s0, s1, s2, s3, w0, w1;\n\t"
-        ".reg .u64 p00, p01, p11;\n\t"
-        "mov.u32        a0, %4;\n\t"
-        "mov.u32        a1, %5;\n\t"
-        "shl.b32        d1, a1, 1;\n\t"
-        "mul.wide.u32   p00, a0, a0;\n\t"
-        "mul.wide.u32   p01, a0, d1;\n\t"
-        "mul.wide.u32   p11, a1, a1;\n\t"
-        "mov.b64        {s0, s1}, p00;\n\t"
-        "mov.b64        {w0, w1}, p01;\n\t"
-        "mov.b64        {s2, s3}, p11;\n\t"
-        "add.cc.u32     s1, s1, w0;\n\t"
-        "addc.cc.u32    s2, s2, w1;\n\t"
-        "addc.u32       s3, s3, 0;\n\t"
-        "mov.u32        %0, s0;\n\t"
-        "mov.u32        %1, s1;\n\t"
-        "mov.u32        %2, s2;\n\t"
-        "mov.u32        %3, s3;\n\t"
-        "}"
-        : "=r"(t0), "=r"(t1), "=r"(t2), "=r"(t3)
-        : "r"(x0), "r"(x1));
-  }
+  // T = x0^2 + (x0 * 2 x1) 2^32 + x1^2 2^64
+  asm("{\n\t"
+      ".reg .u32 a0, a1, d1, s0, s1, s2, s3, w0, w1;\n\t"
+      ".reg .u64 p00, p01, p11;\n\t"
+      "mov.u32        a0, %4;\n\t"
+      "mov.u32        a1, %5;\n\t"
+      "shl.b32        d1, a1, 1;\n\t"
+      "mul.wide.u32   p00, a0, a0;\n\t"
+      "mul.wide.u32   p01, a0, d1;\n\t"
+      "mul.wide.u32   p11, a1, a1;\n\t"
+      "mov.b64        {s0, s1}, p00;\n\t"
+      "mov.b64        {w0, w1}, p01;\n\t"
+      "mov.b64        {s2, s3}, p11;\n\t"
+      "add.cc.u32     s1, s1, w0;\n\t"
+      "addc.cc.u32    s2, s2, w1;\n\t"
+      "addc.u32       s3, s3, 0;\n\t"
+      "mov.u32        %0, s0;\n\t"
+      "mov.u32        %1, s1;\n\t"
+      "mov.u32        %2, s2;\n\t"
+      "mov.u32        %3, s3;\n\t"
+      "}"
+      : "=r"(t0), "=r"(t1), "=r"(t2), "=r"(t3)
+      : "r"(x0), "r"(x1));
   if (do_shift) {  // window multiply by 2^s, s < 32
     t3 = __funnelshift_l(t2, t3, s);
     t2 = __funnelshift_l(t1, t2, s);
@@ -204,6 +184,78 @@ __device__ __forceinline__ void sqr_shift_redc64(uint32_t& x0, uint32_t& x1, uin
       "}"
       : "=r"(r0), "=r"(r1)
       : "r"(t0), "r"(t1), "r"(t2), "r"(t3), "r"(M.m0), "r"(M.m1), "r"(M.mp));
+  x0 = r0;
+  x1 = r1;
+}
+
+// Squaring for moduli of at most 46 bits with a lazy x < 2m < 2^47:
+//   T = x^2 < 2^94 fits three words (x1^2 < 2^30 needs only its low word), and
+//   T' = (T + u m)/2^32 < 2^62 + 2^46 fits two words;
+// the window shift is applied to T' (two words -> three) instead of T, and the
+// second step reduces T' 2^s: (T' 2^s + u' m)/2^32 = (T 2^s + (u 2^s + u' 2^32) m)/2^64,
+// a Montgomery reduction of x^2 2^s with another multiple of m, below 2m while
+// bitlen(m) + s <= 61.  2 x1 is formed by a funnel shift, and the cross product
+// and both reductions are summed in 32-bit carry chains.
+__device__ __forceinline__ void sqr_redc64_p1(uint32_t& x0, uint32_t& x1, uint32_t s, const Mod64& M,
+                                              bool do_shift) {
+  uint32_t y0, y1, y2 = 0;
+  asm("{\n\t"
+      ".reg .u32 a0, a1, d1, s0, h0, b0, b1, q0, u, h, z0, z1, n0, n1, np, cy;\n\t"
+      ".reg .u64 p;\n\t"
+      "mov.u32        a0, %2;\n\t"
+      "mov.u32        a1, %3;\n\t"
+      "mov.u32        n0, %4;\n\t"
+      "mov.u32        n1, %5;\n\t"
+      "mov.u32        np, %6;\n\t"
+      "shf.l.wrap.b32 d1, 0, a1, 1;\n\t"       // 2 x1 (x1 < 2^15)
+      "mul.wide.u32   p, a0, a0;\n\t"
+      "mov.b64        {s0, h0}, p;\n\t"
+      "mul.wide.u32   p, a0, d1;\n\t"
+      "mov.b64        {b0, b1}, p;\n\t"
+      "mul.lo.u32     q0, a1, a1;\n\t"
+      "mul.lo.u32     u, s0, np;\n\t"
+      "mul.hi.u32     h, u, n0;\n\t"
+      "mul.wide.u32   p, u, n1;\n\t"
+      "mov.b64        {z0, z1}, p;\n\t"
+      // T' = h0 + (b1:b0) + q0 2^32 + (z1:z0) + h + (s0 != 0)
+      "add.cc.u32     cy, s0, -1;\n\t"         // carry out = (s0 != 0)
+      "addc.cc.u32    h0, h0, b0;\n\t"
+      "addc.u32       b1, b1, q0;\n\t"
+      "add.cc.u32     h0, h0, z0;\n\t"
+      "addc.u32       b1, b1, z1;\n\t"
+      "add.cc.u32     %0, h0, h;\n\t"
+      "addc.u32       %1, b1, 0;\n\t"
+      "}"
+      : "=r"(y0), "=r"(y1)
+      : "r"(x0), "r"(x1), "r"(M.m0), "r"(M.m1), "r"(M.mp));
+  if (do_shift) {  // T' 2^s on three words, s < 16
+    y2 = __funnelshift_l(y1, 0u, s);
+    y1 = __funnelshift_l(y0, y1, s);
+    y0 <<= s;
+  }
+  uint32_t r0, r1;
+  asm("{\n\t"
+      ".reg .u32 u, h, b0, b1, b2, z0, z1, n0, n1, np, cy;\n\t"
+      ".reg .u64 p;\n\t"
+      "mov.u32        b0, %2;\n\t"
+      "mov.u32        b1, %3;\n\t"
+      "mov.u32        b2, %4;\n\t"
+      "mov.u32        n0, %5;\n\t"
+      "mov.u32        n1, %6;\n\t"
+      "mov.u32        np, %7;\n\t"
+      "mul.lo.u32     u, b0, np;\n\t"
+      "mul.hi.u32     h, u, n0;\n\t"
+      "mul.wide.u32   p, u, n1;\n\t"
+      "mov.b64        {z0, z1}, p;\n\t"
+      // (b2 : b1) + (z1:z0) + h + (b0 != 0) < 2m
+      "add.cc.u32     cy, b0, -1;\n\t"
+      "addc.cc.u32    b1, b1, z0;\n\t"
+      "addc.u32       b2, b2, z1;\n\t"
+      "add.cc.u32     %0, b1, h;\n\t"
+      "addc.u32       %1, b2, 0;\n\t"
+      "}"
+      : "=r"(r0), "=r"(r1)
+      : "r"(y0), "r"(y1), "r"(y2), "r"(M.m0), "r"(M.m1), "r"(M.mp));
   x0 = r0;
   x1 = r1;
 }
@@ -272,11 +324,16 @@ __device__ __forceinline__ void hensel_digits64(uint32_t x0, uint32_t x1, const 
 
 // ---------------------------------------------------------------- 32-bit Montgomery
 //
-// m < 2^29 odd, R = 2^32.  Invariant x < 2m; REDC(x^2 2^s) < 2m while bitlen(m) + s <= 30.
+// m < 2^31 odd, R = 2^32, one word.  Lazy residues (REDUCED = false, m < 2^29):
+// x < 2m, and REDC(x^2 2^s) < 2m while bitlen(m) + s <= 30.  Reduced residues
+// (REDUCED = true, moduli of 30 and 31 bits): x < m after one conditional
+// subtraction per squaring, so x^2 2^s < m^2 2^s fits 64 bits and REDC stays below
+// 2m while bitlen(m) + s <= 32.
 struct Mod32 {
   uint32_t m, mp;
 };
 
+template <bool REDUCED>
 __device__ __forceinline__ uint32_t sqr_shift_redc32(uint32_t x, uint32_t s, const Mod32& M, bool do_shift) {
   uint64_t T = static_cast<uint64_t>(x) * x;  // one 32x32->64 product
   if (do_shift) T <<= s;
@@ -284,7 +341,9 @@ __device__ __forceinline__ uint32_t sqr_shift_redc32(uint32_t x, uint32_t s, con
   const uint32_t t1 = hi32(T);
   const uint32_t u = t0 * M.mp;
   // t0 + lo(u m) = 0 (mod 2^32): the carry out of that word is (t0 != 0)
-  return t1 + __umulhi(u, M.m) + (t0 != 0u ? 1u : 0u);
+  const uint32_t r = t1 + __umulhi(u, M.m) + (t0 != 0u ? 1u : 0u);
+  // r < 2m < 2^32: r - m wraps above r exactly when r < m
+  return REDUCED ? min(r, r - M.m) : r;
 }
 
 template <int N>

@@ -46,7 +46,11 @@ constexpr int kHeadThreads = 256;
 // kernels; a query with W/32 limbs uses the smallest class that holds them.
 constexpr int kLmaxClasses[] = {3, 4, 6, 10, 16, 24, 40};
 constexpr int kNumLmaxClasses = static_cast<int>(sizeof(kLmaxClasses) / sizeof(kLmaxClasses[0]));
-constexpr int kQueueVariants = kNumLmaxClasses * 3;  // limb class x modulus path
+// Modulus paths: 0 one word, lazy residues (bitlen(m) <= 29); 1 two words, three-word
+// square (bitlen <= 46); 2 two words, four-word square (bitlen <= 60); 3 one word,
+// fully reduced residues (bitlen 30 or 31).
+constexpr int kNumPaths = 4;
+constexpr int kQueueVariants = kNumLmaxClasses * kNumPaths;  // limb class x modulus path
 
 // ---------------------------------------------------------------- batches
 //
@@ -81,8 +85,8 @@ struct BatchDev {
 };
 
 // Launch helpers (defined in bbp_kernels.cu).  They return cudaGetLastError().
-// path: 0 = 32-bit moduli (bitlen <= 29), 1 = 64-bit moduli with bitlen <= 47,
-//       2 = 64-bit moduli with bitlen <= 60.
+// path: 0 = one-word moduli, bitlen <= 29; 1 = two-word moduli, bitlen <= 46;
+//       2 = two-word moduli, bitlen <= 60; 3 = one-word moduli of 30 or 31 bits.
 // threads: CTA size, a multiple of 32 in [32, kHeadThreads] (else cudaErrorInvalidValue).
 cudaError_t launch_head(const HeadArgs& a, int path, int streams, int lmax, int blocks, cudaStream_t s,
                         int threads = kHeadThreads);
@@ -105,6 +109,22 @@ int queue_occupancy(int path, int streams, int lmax);
 int head_lmax_for(int L, int bump = 0);
 // Resident CTAs per SM of that instantiation at `threads` per CTA.
 int head_occupancy(int path, int streams, int lmax, int threads = kHeadThreads);
+// Per accumulator class (bbp_lmax*.cu): the launchers the dispatchers above call.
+#define BBP_DECLARE_LMAX(L)                                                                                    \
+  cudaError_t launch_head_l##L(const HeadArgs& a, int path, int streams, int blocks, int threads, cudaStream_t s); \
+  int head_occupancy_l##L(int path, int streams, int threads);                                                 \
+  cudaError_t launch_queue_l##L(const BatchDev& b, uint32_t jb, uint32_t je, unsigned int* cursor, int path,      \
+                                int streams, int blocks, cudaStream_t s);                                      \
+  int queue_occupancy_l##L(int path, int streams);
+BBP_DECLARE_LMAX(3)
+BBP_DECLARE_LMAX(4)
+BBP_DECLARE_LMAX(6)
+BBP_DECLARE_LMAX(10)
+BBP_DECLARE_LMAX(16)
+BBP_DECLARE_LMAX(24)
+BBP_DECLARE_LMAX(40)
+#undef BBP_DECLARE_LMAX
+
 cudaError_t launch_imad_probe(int kind, int blocks, int threads, int iters, unsigned long long* cycles_out,
                               uint32_t* smid_out, uint32_t* sink, cudaStream_t s);
 

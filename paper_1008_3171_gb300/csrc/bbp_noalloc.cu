@@ -95,17 +95,21 @@ extern "C" bbp_status bbp_partial_sum_noalloc(bbp_formula f, uint32_t denominato
 
   if (launch_zero_slots(slots, static_cast<int>(L), st) != cudaSuccess) return BBP_ECUDA;
 
-  // head terms: at most two launches, 32-bit moduli below 2^29 then 64-bit moduli
+  // head terms: one launch per modulus path the range touches (bit lengths up to 29,
+  // 30-31, 32-46, 47-60), each with the window parameters of its largest modulus and
+  // the term pairs per thread of a plan with default settings
   const uint64_t h0 = std::max(k_begin, s.b == 1 ? uint64_t{1} : uint64_t{0});
   const uint64_t h1 = std::min(hi, he);
   if (h0 < h1) {
-    const uint64_t k_wide = first_k_with_bits(kWideMinBits, s.a, s.b);
-    const uint64_t cuts[3] = {h0, std::min(std::max(k_wide, h0), h1), h1};
-    for (int part = 0; part < 2; ++part) {
+    const uint32_t first_bits[3] = {kLazyMaxBits + 1, kWideMinBits, kSmallMaxBits + 1};  // paths 3, 1, 2
+    uint64_t cuts[5] = {h0, h0, h0, h0, h1};
+    for (int i = 0; i < 3; ++i) cuts[i + 1] = std::min(std::max(first_k_with_bits(first_bits[i], s.a, s.b), h0), h1);
+    for (int part = 0; part < 4; ++part) {
       const uint64_t kb = cuts[part], ke = cuts[part + 1];
       if (kb >= ke) continue;
       const int lbits = bitlen(static_cast<uint64_t>(s.a) * (ke - 1) + s.b);
-      const int path = part == 0 ? 0 : path_for_bits(lbits);
+      const int path = path_for_bits(lbits);
+      const int streams = path == 1 ? 2 : 1;
       uint8_t window, first;
       window_params(path, lbits, &window, &first);
       HeadArgs a{};
@@ -124,12 +128,12 @@ extern "C" bbp_status bbp_partial_sum_noalloc(bbp_formula f, uint32_t denominato
       a.window = window;
       a.first = first;
       a.slots = slots;
-      const uint64_t tile = 32ull * kRun;
+      const uint64_t tile = 32ull * static_cast<uint64_t>(streams) * kRun;
       const uint64_t ntiles = (a.count + tile - 1) / tile;
       const uint64_t want = (ntiles + kHeadThreads / 32 - 1) / (kHeadThreads / 32);
-      const uint64_t cap = static_cast<uint64_t>(head_occupancy(path, 1, lmax)) * static_cast<uint64_t>(sms);
+      const uint64_t cap = static_cast<uint64_t>(head_occupancy(path, streams, lmax)) * static_cast<uint64_t>(sms);
       const int blocks = static_cast<int>(std::max<uint64_t>(1, std::min(want, cap)));
-      if (launch_head(a, path, 1, lmax, blocks, st) != cudaSuccess) return BBP_ECUDA;
+      if (launch_head(a, path, streams, lmax, blocks, st) != cudaSuccess) return BBP_ECUDA;
     }
   }
   // tail terms

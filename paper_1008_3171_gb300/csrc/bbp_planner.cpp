@@ -65,31 +65,35 @@ uint64_t natural_end(const FormulaDef& f, uint32_t j, uint64_t d, uint32_t W) {
 }
 
 void window_params(int path, int lbits, uint8_t* window, uint8_t* first) {
-  // shifted reduction keeps x < 2m while lbits + s <= 61 (64-bit) / <= 30 (32-bit);
-  // the first window (x = (R mod m) << w0) needs lbits + 2 w0 + 1 <= 64 / 32, and on
-  // path 1 also x < 2^48 (x1^2 < 2^32), i.e. lbits + w0 <= 48.
-  const bool wide = path > 0;
-  const int shift_cap = wide ? 61 - lbits : 30 - lbits;
+  // A squaring with a window shift s keeps its result below 2m while
+  //   path 0 (one word, lazy x < 2m):      lbits + s <= 30
+  //   path 3 (one word, reduced x < m):    lbits + s <= 32
+  //   paths 1, 2 (two words, lazy x < 2m): lbits + s <= 61
+  // and s <= 2^window - 1.  The first window starts from x = (R mod m) << w0 < m 2^w0,
+  // w0 <= 2^first - 1, and the squaring after it (general routine on paths 1 and 2,
+  // shift at most one bit) needs lbits + 2 w0 + 1 <= 32 (one word) / 64 (two words).
+  const bool wide = path == 1 || path == 2;
+  const int shift_cap = path == 0 ? 30 - lbits : path == 3 ? 32 - lbits : 61 - lbits;
   const int rbits = wide ? 64 : 32;
   int w = 0;
   while (w < 4 && (1 << (w + 1)) - 1 <= shift_cap) ++w;
   int h = 0;
-  while (h < 4 && lbits + 2 * ((1 << (h + 1)) - 1) + 1 <= rbits &&
-         (path != 1 || lbits + (1 << (h + 1)) - 1 <= 48))
-    ++h;
+  while (h < 4 && lbits + 2 * ((1 << (h + 1)) - 1) + 1 <= rbits) ++h;
   *window = static_cast<uint8_t>(w);
   *first = static_cast<uint8_t>(h);
 }
 
 int path_for_bits(int lbits, int wide_min_bits) {
-  return lbits < std::min(wide_min_bits, kWideMinBits) ? 0 : (lbits <= kSmallMaxBits ? 1 : 2);
+  if (lbits < std::min(wide_min_bits, kWideMinBits)) return lbits <= kLazyMaxBits ? 0 : 3;
+  return lbits <= kSmallMaxBits ? 1 : 2;
 }
 
 double head_term_imad(int path, int nb, int first, int lmax) {
   const int h = nb > 0 ? std::min(first, nb - 1) : 0;
   const int sq = nb - h;
-  if (path == 0) return 4.0 * sq + 2.0 * lmax + 8.0;
-  return (path == 1 ? 13.0 : 14.0) * sq + 4.0 * lmax + 8.0;
+  if (path == 0 || path == 3) return 4.0 * sq + 2.0 * lmax + 6.0;
+  if (path == 1) return 13.0 * sq + (sq > 0 ? 1.0 : 0.0) + 4.0 * lmax + 6.0;
+  return 14.0 * sq + 4.0 * lmax + 6.0;
 }
 
 void shard_range(const FormulaDef& f, uint32_t j, uint64_t n, uint32_t W, uint32_t shard, uint32_t nshards,
@@ -107,7 +111,7 @@ void shard_range(const FormulaDef& f, uint32_t j, uint64_t n, uint32_t W, uint32
 
 namespace {
 double range_imad(const FormulaDef& f, const SeriesDef& s, uint64_t d, uint32_t W, const TermRange& r, int lmax) {
-  const int rb = r.path ? 64 : 32;
+  const int rb = (r.path == 1 || r.path == 2) ? 64 : 32;
   const int64_t v0 = static_cast<int64_t>(d) + s.c + static_cast<int64_t>(W) - rb;  // v at k = 0
   const int64_t k_lo = static_cast<int64_t>(r.k_begin);
   const int64_t k_hi = static_cast<int64_t>(r.k_begin + r.count) - 1;

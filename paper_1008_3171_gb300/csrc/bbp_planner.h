@@ -24,12 +24,13 @@ struct FormulaDef {
 const FormulaDef& formula_def(int f);
 
 constexpr uint32_t kMaxWorkingBits = 1280;   // 40 limbs
-constexpr int kWideMinBits = 30;             // moduli with bitlen >= 30 take a 64-bit path
+constexpr int kWideMinBits = 32;             // moduli with bitlen >= 32 take a two-word path
+constexpr int kLazyMaxBits = 29;             // one-word moduli up to this bitlen keep lazy residues (path 0)
 // Lowest allowed crossover: moduli on the 64-bit path are >= 2^(kWideFloorBits-1) = 16,
 // so floor(2^64 / m) * a (a <= 10), formed when R mod m is carried to the next k,
 // stays below 2^64.
 constexpr int kWideFloorBits = 5;
-constexpr int kSmallMaxBits = 47;            // 64-bit path 1 (x1^2 < 2^32) up to this bitlen
+constexpr int kSmallMaxBits = 46;            // two-word path 1 (three-word square) up to this bitlen
 constexpr int kMaxModulusBits = 60;          // 64-bit path bound
 // The persistent queue kernels add one 32-bit partial sum per hand-out (at least
 // one warp tile) to a query's 64-bit carry-save limbs; a query of fewer than this
@@ -43,7 +44,8 @@ constexpr uint32_t kMaxQueueQueries = 1u << 24;
 struct TermRange {
   uint32_t j;         // series index
   uint8_t tail;       // 0 head (e >= 0), 1 tail (e < 0)
-  uint8_t path;       // head: 0 32-bit moduli, 1 64-bit (bitlen <= 47), 2 64-bit
+  uint8_t path;       // head: 0 one word (bitlen <= 29), 1 two words (<= 46), 2 two words (<= 60),
+                      //       3 one word, reduced residues (30, 31)
   uint8_t window;     // head: ladder window bits
   uint8_t first;      // head: first-window bits
   uint64_t k_begin;   // first k
@@ -60,10 +62,11 @@ bool working_bits(uint32_t P, uint32_t G, uint32_t* W);
 uint64_t head_end(const FormulaDef& f, uint32_t j, uint64_t d);
 uint64_t natural_end(const FormulaDef& f, uint32_t j, uint64_t d, uint32_t W);
 
-// Kernel path for moduli of `lbits` bits: 0 (32-bit Montgomery) below
-// `wide_min_bits`, else 1 or 2 (64-bit).  wide_min_bits may be lowered from
-// kWideMinBits down to kWideFloorBits (a tuning choice: small moduli on the 64-bit
-// path) but not raised.
+// Kernel path for moduli of `lbits` bits: one-word Montgomery below
+// `wide_min_bits` (path 0 up to kLazyMaxBits, path 3 for 30 and 31 bits), else a
+// two-word path (1 up to kSmallMaxBits, 2 above).  wide_min_bits may be lowered from
+// kWideMinBits down to kWideFloorBits (a tuning choice: small moduli on the two-word
+// paths) but not raised.
 int path_for_bits(int lbits, int wide_min_bits = kWideMinBits);
 
 // Ladder parameters for moduli of at most `lbits` bits on the given path.
@@ -71,11 +74,12 @@ void window_params(int path, int lbits, uint8_t* window, uint8_t* first);
 
 // Algorithmic work of one head term whose ladder exponent has nb bits, counted as
 // 32-bit halves of 32x32-bit products (the low or high word of a product; a full
-// 64-bit product counts 2).  64-bit moduli: per Montgomery squaring 5 (x0^2 and
-// x0*2x1 in full, x1^2 low word; 6 when x1^2 needs its high word) plus per
-// reduction step 4 (u = T0 m', high word of u m0, u m1 in full) twice; per quotient
-// digit 4; plus 8 for m^-1 mod 2^32.  32-bit moduli: 4 per squaring (x^2 in full,
-// u, high word of u m), 2 per digit, 8 for the inverse.
+// 64-bit product counts 2).  Two-word moduli: per Montgomery squaring 5 (x0^2 and
+// x0*2x1 in full, x1^2 low word; 6 when x1^2 needs its high word: every squaring
+// of path 2 and the first squaring of path 1) plus per reduction step 4 (u = T0 m',
+// high word of u m0, u m1 in full) twice; per quotient digit 4; plus 6 for
+// m^-1 mod 2^32 (three lifting steps).  One-word moduli: 4 per squaring (x^2 in
+// full, u, high word of u m), 2 per digit, 6 for the inverse.
 double head_term_imad(int path, int nb, int first, int lmax);
 
 // Shard `shard` of `nshards` of series j: the head [0, head_end) is cut evenly,

@@ -93,7 +93,7 @@ bbp_status bbp_plan_create(bbp_plan* out, const bbp_plan_opts* opts) {
   p->accum_budget = o.accum_mem_budget ? o.accum_mem_budget : (64u << 20);
   p->max_slots = o.max_slots ? o.max_slots : 4096u;
   p->run = kDefaultRun;
-  p->streams = 1;
+  p->streams = 0;
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, o.device) != cudaSuccess) {
     delete p;
@@ -215,8 +215,8 @@ bbp_status launch_ranges(bbp_plan p, int f, uint64_t n, uint32_t W, const std::v
     a.window = r.window;
     a.first = r.first;
     a.slots = slots;
-    const int streams = p->streams;
-    const uint64_t tile = 32ull * streams * a.run;
+    const int streams = head_streams(p, r.path);
+    const uint64_t tile = tile_terms(p, r.path);
     const uint64_t ntiles = (r.count + tile - 1) / tile;
     const int warps_per_block = p->cta / 32;
     const int occ = head_occupancy(r.path, streams, lmax, p->cta);

@@ -19,9 +19,9 @@ struct bbp_plan_s {
   size_t accum_budget = 0;
   uint32_t max_slots = 0;
   int sm_count = 0;
-  // head-kernel tuning (terms per stream run, streams per thread)
+  // head-kernel tuning (terms per stream run; term pairs per thread, 0 = by path)
   int run = 64;
-  int streams = 1;
+  int streams = 0;
   int grab = 4;  // batched pass: warp tiles handed out per queue operation
   int cta = 256;  // single-query head launches: threads per CTA (multiple of 32, <= 256)
   int limb_bump = 0;  // single-query head launches: accumulator limb class this many sizes above the smallest
@@ -40,6 +40,15 @@ struct bbp_plan_s {
 };
 
 namespace bbp {
+
+// Term pairs per thread of the head and queue kernels on a modulus path: the tune
+// table's value, else two on path 1 (the three-word squaring has the registers for
+// a second independent pair at three CTAs per SM) and one elsewhere.
+inline int head_streams(const bbp_plan_s* p, int path) { return p->streams > 0 ? p->streams : (path == 1 ? 2 : 1); }
+// Terms of one warp tile on that path.
+inline uint64_t tile_terms(const bbp_plan_s* p, int path) {
+  return 32ull * static_cast<uint64_t>(head_streams(p, path)) * static_cast<uint64_t>(p->run);
+}
 
 bbp_status cuda_status(cudaError_t e);
 bbp_status plan_query(bbp_plan p, int f, uint64_t n, uint32_t W, int j_only, uint64_t k_lo, uint64_t k_hi,

@@ -82,6 +82,7 @@ struct Work {
   bool tail;
   int variant;
   uint64_t tiles;  // head: warp tiles of the range
+  uint64_t tile;   // head: terms per warp tile on the range's path
   HeadArgs head;
   TailArgs tailargs;
 };
@@ -178,7 +179,6 @@ bbp_status plan_query_work(bbp_plan p, uint64_t n, uint32_t P, Query* q) {
     if (st != 0) return BBP_EINVAL;
     N += natural_end(F, j, n - 1, W);
   }
-  const uint64_t tile = 32ull * p->streams * p->run;
   q->n = n;
   q->P = P;
   q->W = W;
@@ -218,8 +218,9 @@ bbp_status plan_query_work(bbp_plan p, uint64_t n, uint32_t P, Query* q) {
       a.run = static_cast<uint32_t>(p->run);
       a.window = r.window;
       a.first = r.first;
-      w.tiles = (r.count + tile - 1) / tile;
-      w.variant = lmax_index(lmax) * 3 + r.path;
+      w.tile = tile_terms(p, r.path);
+      w.tiles = (r.count + w.tile - 1) / w.tile;
+      w.variant = lmax_index(lmax) * kNumPaths + r.path;
     }
     q->work.push_back(w);
   }
@@ -246,14 +247,13 @@ struct Piece {
   uint32_t slot;
 };
 
-// Takes up to `budget_tiles` tiles (at least one item) of q's remaining work.
-void take_pieces(ServeEngine* E, Query* q, uint64_t budget_tiles, std::vector<Piece>& out, uint64_t* terms) {
-  bbp_plan p = E->plan;
-  const uint64_t tile = 32ull * p->streams * p->run;
+// Takes about `budget_terms` terms (at least one item) of q's remaining work, in
+// whole warp tiles of each range.
+void take_pieces(ServeEngine* E, Query* q, uint64_t budget_terms, std::vector<Piece>& out, uint64_t* terms) {
   const FormulaDef& F = formula_def(BBP_BELLARD);
   unsigned long long* slots = E->d_accum + static_cast<uint64_t>(q->slot) * kMaxLimbs;
   bool first = true;
-  while (q->next < q->work.size() && (first || budget_tiles > 0)) {
+  while (q->next < q->work.size() && (first || budget_terms > 0)) {
     first = false;
     Work& w = q->work[q->next];
     Piece pc{};
@@ -263,12 +263,13 @@ void take_pieces(ServeEngine* E, Query* q, uint64_t budget_tiles, std::vector<Pi
       pc.tailargs = w.tailargs;
       pc.tailargs.slots = slots;
       *terms += w.tailargs.count;
-      budget_tiles = budget_tiles > 0 ? budget_tiles - 1 : 0;
+      budget_terms = budget_terms > w.tailargs.count ? budget_terms - w.tailargs.count : 0;
       ++q->next;
       q->tile_off = 0;
     } else {
+      const uint64_t tile = w.tile;
       const uint64_t avail = w.tiles - q->tile_off;
-      const uint64_t take = std::max<uint64_t>(1, std::min(avail, budget_tiles));
+      const uint64_t take = std::max<uint64_t>(1, std::min(avail, budget_terms / tile));
       HeadArgs a = w.head;
       a.k_begin = w.head.k_begin + q->tile_off * tile;
       const uint64_t end = std::min(w.head.k_begin + w.head.count, a.k_begin + take * tile);
@@ -280,7 +281,7 @@ void take_pieces(ServeEngine* E, Query* q, uint64_t budget_tiles, std::vector<Pi
       pc.variant = w.variant;
       pc.tiles = (a.count + tile - 1) / tile;
       *terms += a.count;
-      budget_tiles = budget_tiles > take ? budget_tiles - take : 0;
+      budget_terms = budget_terms > take * tile ? budget_terms - take * tile : 0;
       q->tile_off += take;
       if (q->tile_off >= w.tiles) {
         ++q->next;
@@ -353,10 +354,8 @@ void free_engine(ServeEngine* E) {
 // last piece is in it move to H.finishing.  Returns false on a CUDA error.
 bool enqueue_iteration(ServeEngine* E, HostStage& H, std::vector<Query*>& batch, std::vector<int>& fresh_slots) {
   bbp_plan p = E->plan;
-  const uint64_t tile = 32ull * p->streams * p->run;
-  const uint64_t budget_terms = static_cast<uint64_t>(E->rate * kIterTargetSeconds);
-  const uint64_t budget_tiles = std::max<uint64_t>(1, budget_terms / tile);
-  const uint64_t share = std::max<uint64_t>(1, budget_tiles / std::max<size_t>(1, batch.size()));
+  const uint64_t budget_terms = std::max<uint64_t>(1, static_cast<uint64_t>(E->rate * kIterTargetSeconds));
+  const uint64_t share = std::max<uint64_t>(1, budget_terms / std::max<size_t>(1, batch.size()));
   std::vector<Piece> pieces;
   uint64_t terms = 0;
   std::vector<uint32_t> npieces(batch.size(), 0);
@@ -442,9 +441,9 @@ bool enqueue_iteration(ServeEngine* E, HostStage& H, std::vector<Query*>& batch,
   chk(launch_queue_tail(dev, 0, static_cast<uint32_t>(nt), E->d_cursors + kVariants, p->sm_count * 4, s));
   for (int v = 0; v < kVariants; ++v) {
     if (vb[v] == vb[v + 1]) continue;
-    const int lmax = kLmaxClasses[v / 3], path = v % 3;
-    const int blocks = queue_occupancy(path, p->streams, lmax) * p->sm_count;
-    chk(launch_queue(dev, vb[v], vb[v + 1], E->d_cursors + v, path, p->streams, lmax, blocks, s));
+    const int lmax = kLmaxClasses[v / kNumPaths], path = v % kNumPaths;
+    const int blocks = queue_occupancy(path, head_streams(p, path), lmax) * p->sm_count;
+    chk(launch_queue(dev, vb[v], vb[v + 1], E->d_cursors + v, path, head_streams(p, path), lmax, blocks, s));
   }
   if (!H.finishing.empty()) {  // results of the queries that finish in this iteration
     chk(cudaMemcpyAsync(H.out, E->d_out, static_cast<size_t>(kOutStride) * E->max_slots, cudaMemcpyDeviceToHost, s));

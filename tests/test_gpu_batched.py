@@ -1,5 +1,6 @@
-"""The batched persistent pass (bbp_bits_batch) against the oracle and against the
-single-query path, bit for bit, on seeded mixed-size batches."""
+"""The batched persistent pass (bbp_bits_batch) against the oracle (and, for
+queries too large to run through the oracle here, the paper's printed rows and
+the single-query path), bit for bit, on seeded mixed-size batches."""
 
 import pytest
 
@@ -38,6 +39,20 @@ def test_batch_matches_single_query_path(bbp, plan):
     vals, valid, _ = bbp.bbp_bits_batch(plan.handle, 0, ns, Ps)
     for q, (n, P) in enumerate(zip(ns, Ps)):
         assert (vals[q], valid[q]) == plan.bits(n, P), (q, n, P)
+        if n < 2 * 10**6:
+            assert (vals[q], valid[q]) == oracle.c_bits(n, P, 64), (q, n, P)
+
+
+def test_large_queries_in_a_batch_match_oracle(bbp, plan):
+    """Queries of n = 1e7 .. 6e7 (moduli up to 2^29.2: both one-limb paths) among
+    small ones, each checked against the oracle in full."""
+    ns, Ps = workloads.batched_queries(count=24, seed=19, lo=3.0, hi=6.0)
+    big = [10**7 + 1, 23_456_789, 41_234_567, 59_999_999]
+    ns += big
+    Ps += [256, 64, 128, 256]
+    vals, valid, _ = bbp.bbp_bits_batch(plan.handle, 0, ns, Ps)
+    for q, (n, P) in enumerate(zip(ns, Ps)):
+        assert (vals[q], valid[q]) == oracle.c_bits(n, P, 64), (q, n, P)
 
 
 def test_batch_against_paper_rows(bbp, plan, pins):

@@ -1,15 +1,18 @@
 """Checkpoint / resume of a long query (the paper persists partial sums so a run
 can be killed and resumed, Sec. 4): the carry-save accumulators after some
 shards are the checkpoint; a new plan restores them, adds the remaining shards
-and finalizes, and the bits equal an uninterrupted run."""
+and finalizes, and the bits equal the oracle's (n = 1e9 + 1: the paper's Table 2
+row for that position, whose first 256 bits the oracle is pinned to)."""
 
 import pytest
+
+import oracle
 
 pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("n,P,shards,stop", [(10**9 + 1, 256, 8, 3), (10**6, 64, 5, 0), (123_457, 1000, 3, 2)])
-def test_resume_from_host_checkpoint(n, P, shards, stop):
+def test_resume_from_host_checkpoint(pins, n, P, shards, stop):
     import torch
 
     import paper_1008_3171_gb300 as bbp
@@ -37,6 +40,13 @@ def test_resume_from_host_checkpoint(n, P, shards, stop):
         torch.cuda.synchronize()
         raw = bytes(out.tolist())
         got = int.from_bytes(raw, "big") >> (8 * len(raw) - P)
-        assert (got, int(valid.item())) == second.bits(n, P)
+        ok = int(valid.item())
+        if n == 10**9 + 1:
+            pin = pins["suppressed_m9"]
+            ref = int(pin["hex"], 16) >> (4 * len(pin["hex"]) - pin["bits"])
+            assert ok == P and got == ref >> (pin["bits"] - P)
+        else:
+            assert (got, ok) == oracle.c_bits(n, P, 64)
+        assert (got, ok) == second.bits(n, P)
     finally:
         second.close()

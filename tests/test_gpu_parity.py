@@ -2,8 +2,8 @@
 
 The accumulator is exact integer arithmetic modulo 2^W, so the tolerance is zero:
 every partial sum, raw accumulator and output bit must equal the oracle's.  Cases
-cover several tiles and ragged tails, the 32-/64-bit modulus paths and their
-boundary, k = 0 (m = 1), the head/tail boundary, the tail end, both formulas,
+cover several tiles and ragged tails, the four modulus paths and every boundary
+between them, k = 0 (m = 1), the head/tail boundary, the tail end, both formulas,
 and sampled ranges at the full configuration sizes (n = 1e9, 1e12, 1e13).
 """
 
@@ -120,7 +120,8 @@ def test_partial_sums_small_n(plan32, plan64, formula):
 
 
 def test_partial_sums_many_tiles(plan64):
-    """Ranges spanning many warp tiles and CTAs with ragged ends, both modulus paths."""
+    """Ranges spanning many warp tiles and CTAs with ragged ends, on the one-limb paths
+    (n = 1e9 + 1: moduli below 2^30)."""
     rng = random.Random(11)
     n, P, G = 10**9 + 1, 128, 64
     for j in range(7):
@@ -141,8 +142,9 @@ def test_partial_sums_full_size_sampled(plan64, n):
         he = o1.head_end(f, s, n - 1)
         ne = o1.natural_end(f, s, n - 1, W)
         starts = [1, he - 4000, rng.randrange(1, he - 5000), rng.randrange(1, he - 5000)]
-        # the 32-/64-bit path boundary (m crosses 2^29)
+        # the one-limb path boundaries (m crosses 2^29 and 2^31)
         starts.append(max(1, ((1 << 29) - s.b) // s.a - 1500))
+        starts.append(max(1, ((1 << 31) - s.b) // s.a - 1500))
         for kb in starts:
             ke = kb + 3001
             got = plan64.partial_sum(0, j, kb, ke, n, P)
@@ -151,6 +153,23 @@ def test_partial_sums_full_size_sampled(plan64, n):
         got = plan64.partial_sum(0, j, he - 10, None, n, P)
         assert got == oracle.c_partial_sum(0, j, he - 10, None, n, P, G)
         assert ne > he
+
+
+@pytest.mark.parametrize("bits", [29, 30, 31, 32, 46, 47])
+def test_modulus_path_boundaries(plan64, bits):
+    """k-ranges whose moduli cross 2^bits, on every series: the one-limb lazy and
+    reduced paths meet at 2^29 (bitlen 30), the reduced one-limb path and the
+    three-word two-limb path at 2^31 (bitlen 32), the three- and four-word two-limb
+    paths at 2^46 (bitlen 47); 2^30 and 2^32 cross inside a path.  n = 2e15 - 3
+    reaches all of them in the head."""
+    n, P, G = 2 * 10**15 - 3, 256, 64
+    f = o1.BELLARD
+    for j, s in enumerate(f.series):
+        k_cross = ((1 << (bits - 1)) - s.b) // s.a
+        for kb, cnt in ((max(1, k_cross - 1500), 3001), (max(1, k_cross - 70_000), 140_001)):
+            got = plan64.partial_sum(0, j, kb, kb + cnt, n, P)
+            want = oracle.c_partial_sum(0, j, kb, kb + cnt, n, P, G)
+            assert got == want, (bits, j, kb, cnt)
 
 
 def test_raw_accumulator_matches_oracle(bbp, plan32, plan64):

@@ -1,6 +1,7 @@
 """Serving (bbp_submit / bbp_poll): continuous batching returns, for every query,
 exactly the bits the query gets alone -- while other queries (a long one and many
-short ones arriving over time) share the GPU with it."""
+short ones arriving over time) share the GPU with it -- and, for every query the
+oracle can run here (n < 4e7, including two of n > 1e7), exactly the oracle's bits."""
 
 import random
 import time
@@ -41,6 +42,8 @@ def test_results_in_the_mix_equal_results_alone(bbp):
         tickets = {}
         long_n, long_P = 10**10 + 1, 256
         tickets[bbp.bbp_submit(plan.handle, long_n, long_P)] = (long_n, long_P)
+        for n_big, P_big in ((12_345_679, 256), (33_333_331, 64)):   # checked against the oracle in full
+            tickets[bbp.bbp_submit(plan.handle, n_big, P_big)] = (n_big, P_big)
         rng = random.Random(21)
         arrivals = workloads.serving_arrivals(40, rate_per_s=200.0, seed=21, lo=2.0, hi=8.0)
         t0 = time.time()
@@ -58,7 +61,7 @@ def test_results_in_the_mix_equal_results_alone(bbp):
         try:
             for t, (n, P) in tickets.items():
                 assert done[t] == alone.bits(n, P), (n, P)
-                if n < 10**7:
+                if n < 4 * 10**7:
                     assert done[t] == oracle.c_bits(n, P, 64), (n, P)
         finally:
             alone.close()
@@ -104,13 +107,13 @@ def test_tickets(bbp):
 def test_query_too_large_for_the_queue_limbs_is_refused(bbp, tmp_path):
     """A query needing 2^32 - 2^24 or more warp tiles could overflow its 64-bit
     carry-save limbs in the queue kernels: bbp_submit and bbp_bits_batch refuse it
-    with BBP_ERANGE while planning, before any launch.  With run = 2 a tile is 64
-    terms, so n = 5e11 (3.5e11 head terms, 5.5e9 tiles) is past the limit and
-    n = 1e11 (1.1e9 tiles) is not."""
+    with BBP_ERANGE while planning, before any launch.  With run = 2 and one term
+    pair per thread a tile is 64 terms, so n = 5e11 (3.5e11 head terms, 5.5e9 tiles)
+    is past the limit and n = 1e11 (1.1e9 tiles) is not."""
     import json
 
     table = tmp_path / "tune.json"
-    table.write_text(json.dumps({"run": 2}))
+    table.write_text(json.dumps({"run": 2, "streams": 1}))
     plan = bbp.Plan(device=0, guard_bits=64, tune_table=str(table))
     try:
         with pytest.raises(bbp.BBPError) as e:

@@ -23,6 +23,9 @@ SETTINGS = [
     {"run": 64, "cta": 64, "limb_bump": 1, "wide_min_bits": 5},
     {"run": 32, "streams": 2, "cta": 128, "wide_min_bits": 17, "grab": 2},
     {"run": 64, "cta": 32, "limb_bump": 2, "wide_min_bits": 29},
+    {"run": 64, "streams": 1, "wide_min_bits": 31},
+    {"run": 128, "streams": 2, "wide_min_bits": 32, "cta": 192},
+    {"run": 8, "wide_min_bits": 30, "grab": 5},
 ]
 
 
@@ -44,7 +47,9 @@ def test_settings_give_identical_sums(setting):
     try:
         for n, P, j, kb, ke in [(10**12, 256, 0, 5 * 10**10, 5 * 10**10 + 70_001),
                                 (10**12, 256, 5, 3, 200_003), (10**9 + 1, 128, 3, 0, None),
-                                (99_991, 64, 6, 0, None), (10**6, 100, 1, 1, 12_345)]:
+                                (99_991, 64, 6, 0, None), (10**6, 100, 1, 1, 12_345),
+                                (3 * 10**9 + 7, 64, 2, 2 * 10**8 - 40_000, 2 * 10**8 + 40_000),
+                                (10**15 + 1, 256, 4, 7_036_874_417_765 - 20_000, 7_036_874_417_765 + 20_000)]:
             assert p.partial_sum(0, j, kb, ke, n, P) == oracle.c_partial_sum(0, j, kb, ke, n, P, 64)
         ns, Ps = workloads.batched_queries(count=48, seed=17, lo=2.0, hi=6.5)
         vals, valid, _ = bbp.bbp_bits_batch(p.handle, 0, ns, Ps)

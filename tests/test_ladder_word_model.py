@@ -4,17 +4,22 @@ extremes of the launch ranges the planner produces.
 The kernels keep every value in 32-bit words and drop carries they have shown
 cannot occur; the GPU parity tests sample terms, this model checks the claims
 themselves.  It restates, word by word, what the device code does for one term
-(in `csrc/bbp_device.cuh` and `process_tile` in `csrc/bbp_kernels.cu`):
-  * -m^-1 mod 2^32 by Newton-Hensel lifting from m (four steps);
+(in `csrc/bbp_device.cuh` and `process_tile` in `csrc/bbp_tile.cuh`):
+  * -m^-1 mod 2^32 by Newton-Hensel lifting from the start (3 m) XOR 2 (three steps);
   * R mod m by bit-serial division, carried to k + 1 with R = q (m + a) + (r - a q);
   * the left-to-right ladder: a first window taken as (R mod m) << w0, then
     groups of `window` bits, each len - 1 plain Montgomery squarings and one
-    squaring with the group's bits shifted into the unreduced square;
-  * 64-bit squaring on two words (the x1^2 high word dropped on path 1), the
+    squaring with the group's bits shifted in;
+  * path 2 (and the first squaring of path 1): the square on four words, the
     shift by funnel shifts, two word-by-word REDC steps with the vanishing low
     word's carry taken as (word != 0) and u m1 accumulated by the multiply;
-  * 32-bit squaring and REDC on one word;
-  * W/32 exact-division digits (Hensel), least significant first.
+  * path 1: the square on three words (x1^2 low word only), the first REDC step
+    summed in 32-bit carry chains into two words, the window shift applied to
+    that two-word value, then the second REDC step;
+  * one-word squaring and REDC, with lazy residues (path 0) or one conditional
+    subtraction per squaring (path 3, moduli of 30 and 31 bits);
+  * W/32 exact-division digits (Hensel), least significant first; a lane past
+    the range enters them with x = 0.
 Every dropped carry, truncated shift and narrowed product is asserted to be
 zero or in range, the ladder result must be 2^E mod m, and the digits must
 equal the oracle's term floor((2^e mod m) 2^W / m) mod 2^W (Eq. 5).  The launch
@@ -48,8 +53,9 @@ def bbp():
 
 
 def neg_inverse32(m0):
-    x = m0
-    for _ in range(4):
+    x = ((3 * m0) ^ 2) & M32
+    assert (x * m0) & 31 == 1                # five correct bits to start
+    for _ in range(3):                       # 5 -> 10 -> 20 -> 40 bits
         x = (x * ((2 - m0 * x) & M32)) & M32
     assert (x * m0) & M32 == 1
     return (-x) & M32
@@ -82,29 +88,20 @@ def r_mod_m_advance(q, r, m_next, a, rbits):
     return q, r2
 
 
-def sqr_shift_redc64(x, s, m, mp, small, do_shift):
+def sqr_shift_redc64(x, s, m, mp, do_shift):
+    """General squaring (path 2 and the first squaring of path 1): four-word square."""
     x0, x1 = x & M32, x >> 32
     assert x1 < 1 << 31                      # d1 = x1 << 1 in one word
     d1 = x1 << 1
-    p00, p01 = x0 * x0, x0 * d1
-    if small:
-        assert x1 * x1 <= M32                # path 1 keeps only the low word of x1^2
-        s1 = (p00 >> 32) + (p01 & M32)
-        c = s1 >> 32
-        s1 &= M32
-        s2 = (p01 >> 32) + (x1 * x1) + c
-        s3 = s2 >> 32
-        s2 &= M32
-    else:
-        p11 = x1 * x1
-        s1 = (p00 >> 32) + (p01 & M32)
-        c = s1 >> 32
-        s1 &= M32
-        s2 = (p11 & M32) + (p01 >> 32) + c
-        c = s2 >> 32
-        s2 &= M32
-        s3 = (p11 >> 32) + c
-        assert s3 <= M32
+    p00, p01, p11 = x0 * x0, x0 * d1, x1 * x1
+    s1 = (p00 >> 32) + (p01 & M32)
+    c = s1 >> 32
+    s1 &= M32
+    s2 = (p11 & M32) + (p01 >> 32) + c
+    c = s2 >> 32
+    s2 &= M32
+    s3 = (p11 >> 32) + c
+    assert s3 <= M32
     s0 = p00 & M32
     T = s0 | s1 << 32 | s2 << 64 | s3 << 96
     assert T == x * x
@@ -140,6 +137,69 @@ def sqr_shift_redc64(x, s, m, mp, small, do_shift):
     return a
 
 
+def add32(a, b, cin=0):
+    """One 32-bit add of a carry chain: (sum mod 2^32, carry out)."""
+    v = a + b + cin
+    return v & M32, v >> 32
+
+
+def sqr_redc64_p1(x, s, m, mp, do_shift):
+    """Path 1 (bitlen(m) <= 46, x < 2m): three-word square, first REDC step into two
+    words by 32-bit carry chains, the window shift on that two-word value, then the
+    second step.  Mirrors the two asm blocks of sqr_redc64_p1."""
+    assert x < 2 * m
+    x0, x1 = x & M32, x >> 32
+    d1 = (x1 << 1) & M32                     # funnel shift of (x1 : 0) by one
+    assert d1 == 2 * x1
+    p00, p01 = x0 * x0, x0 * d1
+    q0 = (x1 * x1) & M32
+    assert x1 * x1 <= M32                    # only the low word of x1^2 is formed
+    s0, h0 = p00 & M32, p00 >> 32
+    b0, b1 = p01 & M32, p01 >> 32
+    m0, m1 = m & M32, m >> 32
+    u = (s0 * mp) & M32
+    assert (s0 + u * m0) & M32 == 0
+    h = (u * m0) >> 32
+    z = u * m1
+    z0, z1 = z & M32, z >> 32
+    _, c = add32(s0, M32)                    # carry out = (s0 != 0)
+    h0, c = add32(h0, b0, c)
+    b1, c2 = add32(b1, q0, c)
+    assert c2 == 0
+    h0, c = add32(h0, z0)
+    b1, c2 = add32(b1, z1, c)
+    assert c2 == 0
+    y0, c = add32(h0, h)
+    y1, c2 = add32(b1, 0, c)
+    assert c2 == 0                           # T' fits two words
+    T = x * x
+    assert y0 | y1 << 32 == (T + u * m) >> 32
+    y2 = 0
+    if do_shift:
+        assert 0 <= s < 32
+        y = (y0 | y1 << 32) << s
+        assert y >> 96 == 0                  # three words after the shift
+        y0, y1, y2 = y & M32, (y >> 32) & M32, y >> 64
+    Y = y0 | y1 << 32 | y2 << 64
+    u2 = (y0 * mp) & M32
+    assert (y0 + u2 * m0) & M32 == 0
+    h2 = (u2 * m0) >> 32
+    z = u2 * m1
+    z0, z1 = z & M32, z >> 32
+    _, c = add32(y0, M32)
+    b1, c = add32(y1, z0, c)
+    b2, c2 = add32(y2, z1, c)
+    assert c2 == 0
+    r0, c = add32(b1, h2)
+    r1, c2 = add32(b2, 0, c)
+    assert c2 == 0
+    r = r0 | r1 << 32
+    assert r == (Y + u2 * m) >> 32
+    assert r % m == (x * x << (s if do_shift else 0)) * pow(2, -64, m) % m
+    assert r < 2 * m
+    return r
+
+
 def hensel_step64(x, m, mp):
     x0, x1 = x & M32, x >> 32
     q = (x0 * mp) & M32
@@ -150,7 +210,9 @@ def hensel_step64(x, m, mp):
     return q, r
 
 
-def sqr_shift_redc32(x, s, m, mp, do_shift):
+def sqr_shift_redc32(x, s, m, mp, do_shift, reduced):
+    if reduced:
+        assert x < m
     T = x * x
     if do_shift:
         T <<= s
@@ -159,12 +221,16 @@ def sqr_shift_redc32(x, s, m, mp, do_shift):
     u = (t0 * mp) & M32
     r = t1 + ((u * m) >> 32) + (1 if t0 else 0)
     assert r <= M32 and r < 2 * m
+    if reduced:                               # min(r, r - m) on 32-bit words
+        r = min(r, (r - m) & M32)
+        assert r < m
     return r
 
 
-def ladder_term(path, window, first, m, E, W, extra, r_mod_m):
+def ladder_term(path, window, first, m, E, W, extra, r_mod_m, valid=True):
     """2^E mod m by the kernel's ladder, then the W-bit quotient digits."""
-    rb = 64 if path else 32
+    wide = path in (1, 2)
+    rb = 64 if wide else 32
     mp = neg_inverse32(m & M32)
     v = E - rb
     assert v >= 0
@@ -175,23 +241,41 @@ def ladder_term(path, window, first, m, E, W, extra, r_mod_m):
     x = r_mod_m << w0
     assert x < 1 << rb
     rem = v & ((1 << low) - 1) if low > 0 else 0
+
+    def square(x, sh, shifted, general=False):
+        if path == 2 or general:
+            return sqr_shift_redc64(x, sh, m, mp, shifted)
+        if path == 1:
+            return sqr_redc64_p1(x, sh, m, mp, shifted)
+        return sqr_shift_redc32(x, sh, m, mp, shifted, path == 3)
+
     p = low
+    if path == 1 and p > 0:                  # first group: its first squaring on the general routine
+        ln = min(window, p)
+        p -= ln
+        sh = (rem >> p) & ((1 << ln) - 1)
+        if ln == 1:
+            x = square(x, sh, True, general=True)
+        else:
+            x = square(x, 0, False, general=True)
+            for i in range(ln - 1):
+                last = i == ln - 2
+                x = square(x, sh if last else 0, last)
     while p > 0:
         ln = min(window, p)
         p -= ln
         for i in range(ln):
             last = i == ln - 1
             sh = ((rem >> p) & ((1 << ln) - 1)) if last else 0
-            if path:
-                x = sqr_shift_redc64(x, sh, m, mp, path == 1, last)
-            else:
-                x = sqr_shift_redc32(x, sh, m, mp, last)
+            x = square(x, sh, last)
     assert x % m == pow(2, E, m)
     if x >= m:
         x -= m
+    if not valid:                            # a lane past the range: x = 0, all digits 0
+        x = 0
     digits = []
     for _ in range(W // 32):
-        if path:
+        if wide:
             q, x = hensel_step64(x, m, mp)
         else:
             q = (x * mp) & M32
@@ -201,30 +285,59 @@ def ladder_term(path, window, first, m, E, W, extra, r_mod_m):
 
 
 CONFIGS = [
-    (0, 10**12, 256, 64, 30),
-    (0, 10**14 + 1, 256, 64, 30),
-    (0, 2 * 10**15 - 3, 256, 64, 30),
-    (0, 10**17 + 1, 64, 32, 30),
-    (1, 10**16 + 7, 1000, 64, 30),
+    (0, 10**12, 256, 64, 32),
+    (0, 10**14 + 1, 256, 64, 32),
+    (0, 2 * 10**15 - 3, 256, 64, 32),
+    (0, 10**17 + 1, 64, 32, 32),
+    (1, 10**16 + 7, 1000, 64, 32),
     (0, 10**7 + 1, 64, 64, 5),
     (0, 10**9 + 1, 128, 64, 17),
+    (0, 10**9 + 1, 128, 64, 32),
+    (0, 3 * 10**9 + 7, 64, 64, 32),
+    (1, 2 * 10**9 + 3, 256, 64, 31),
+    (0, 10**10 + 1, 256, 64, 30),
 ]
+
+
+def test_every_path_is_modelled(bbp):
+    """The configurations reach every modulus path: one word lazy (0) and reduced (3),
+    two words with the three-word square (1) and the four-word square (2)."""
+    seen = set()
+    for cfg in CONFIGS:
+        seen |= _check_config(bbp, *cfg)
+    assert seen == {0, 1, 2, 3}
+
+
+def test_inverse_start_value_is_five_bits():
+    """(3 m) XOR 2 is an inverse of every odd m modulo 2^5 (here: every odd residue mod
+    2^16), and three lifting steps from it reach 32 bits for random odd words."""
+    for m in range(1, 1 << 16, 2):
+        assert (m * ((3 * m) ^ 2)) % 32 == 1
+    rng = random.Random(3)
+    for _ in range(2000):
+        m = rng.randrange(1, 1 << 32) | 1
+        assert (m * neg_inverse32(m)) & M32 == M32      # m (-m^-1) = -1
 
 
 @pytest.mark.parametrize("f,n,P,G,wide", CONFIGS)
 def test_word_model_matches_oracle_at_range_extremes(bbp, f, n, P, G, wide):
+    _check_config(bbp, f, n, P, G, wide)
+
+
+def _check_config(bbp, f, n, P, G, wide):
     rng = random.Random(n ^ (P << 8) ^ wide)
     F = o1.FORMULAS[f]
     W = o1.working_bits(P, G)
     d = n - 1
     ranges, _ = bbp.bbp_explain(f, n, P, G, wide)
     checked = 0
+    paths = set()
     for r in ranges:
         if r["tail"]:
             continue
         s = F.series[r["denominator"]]
         path, window, first = r["path"], r["window"], r["first"]
-        rb = 64 if path else 32
+        rb = 64 if path in (1, 2) else 32
         k_last = r["k_begin"] + r["count"] - 1
         ks = sorted({r["k_begin"], min(r["k_begin"] + 1, k_last), k_last}
                     | {rng.randrange(r["k_begin"], k_last + 1) for _ in range(3)})
@@ -241,13 +354,16 @@ def test_word_model_matches_oracle_at_range_extremes(bbp, f, n, P, G, wide):
             want = o1.term(F, s, d, k, W)
             for extra in (0, 1, 9):               # a warp tile can span E from ~64 to ~20000
                 assert ladder_term(path, window, first, m, E, W, extra, rr) % (1 << W) == want, (f, n, k, extra)
+            assert ladder_term(path, window, first, m, E, W, 0, rr, valid=False) == 0
             # the largest shifts: an all-ones exponent of the same length, at the range's largest modulus
             m_max = s.a * k_last + s.b
             E1 = rb + (1 << max(1, (E - rb).bit_length())) - 1
             x = ladder_term(path, window, first, m_max, E1, 64, 0, (1 << rb) % m_max)
             assert x == (-pow(2, E1, m_max) * pow(m_max, -1, 1 << 64)) % (1 << 64)
             checked += 1
+            paths.add(path)
     assert checked > 0
+    return paths
 
 
 def test_quotient_digits_are_the_exact_division():
