@@ -58,17 +58,20 @@ typedef struct bbp_plan_s* bbp_plan;
 
 typedef struct bbp_plan_opts {
   int device;               /* CUDA device ordinal */
-  void* stream;             /* cudaStream_t for all work; NULL: the plan creates its own */
+  void* stream;             /* cudaStream_t for all work; NULL: the plan creates its own (the legacy
+                               default stream cannot be chosen: its handle is NULL too) */
   uint32_t guard_bits;      /* G: positive multiple of 32; 0 selects 64 */
   size_t accum_mem_budget;  /* bytes of device accumulator memory for queued queries; 0: 64 MiB */
   uint32_t max_slots;       /* concurrent queries admitted by bbp_submit; 0: 4096; at most 2^24 are used */
   const char* tune_table;   /* path of an autotune table or NULL for defaults.  JSON object; keys (others
                                ignored, out-of-range values keep the default): run (even, 2..4096, terms
-                               per stream; 64), streams (1 or 2; 1), cta (head-kernel threads per CTA,
-                               multiple of 32 up to 256; 256), limb_bump (0..2 accumulator classes above
-                               the smallest that holds W; 0), wide_min_bits (5..30: moduli of at least
-                               this many bits use the two-limb Montgomery path; 30), grab (1..1024 warp
-                               tiles per queue operation in batched passes; 4).  None changes a result. */
+                               per stream; 64), streams (1 or 2 term pairs per thread on every modulus
+                               path; default 2 on moduli of 32 to 46 bits, 1 elsewhere), cta (head-kernel
+                               threads per CTA, multiple of 32 up to 256; 256), limb_bump (0..2
+                               accumulator classes above the smallest that holds W; 0), wide_min_bits
+                               (5..32: moduli of at least this many bits use a two-limb Montgomery path;
+                               32), grab (1..1024 warp tiles per queue operation in batched passes; 4).
+                               None changes a result. */
   uint32_t profile;         /* 1: time head-kernel launches with CUDA events (see bbp_stats) */
   uint32_t strict;          /* 1: bbp_bits fails with BBP_EINVALID_BITS unless all P bits certify */
 } bbp_plan_opts;
@@ -147,7 +150,9 @@ bbp_status bbp_shard_range(bbp_formula f, uint32_t denominator, uint64_t n, uint
 typedef struct bbp_range {
   uint32_t denominator;  /* series index j */
   uint32_t tail;         /* 0: head terms (exponent >= 0, modular exponentiation), 1: tail terms */
-  uint32_t path;         /* head: 0 one-limb (32-bit) Montgomery, 1 two-limb for moduli < 2^47, 2 two-limb < 2^60 */
+  uint32_t path;         /* head: Montgomery arithmetic for the range's moduli: 0 one limb (32-bit), moduli
+                            < 2^29; 3 one limb with fully reduced residues, 2^29 <= m < 2^31; 1 two limbs,
+                            three-word square, m < 2^46; 2 two limbs, four-word square, m < 2^60 */
   uint32_t window;       /* head: ladder window bits (a window's multiplication is a shift) */
   uint32_t first;        /* head: bits taken by the first window (no squaring) */
   uint32_t reserved;
@@ -159,12 +164,12 @@ typedef struct bbp_range {
 /* Host-only plan of the whole query at bit position n with P bits and guard_bits
  * guard bits (W = roundup(P, 32) + guard_bits): the launch ranges bbp_bits would
  * run, series by series in k order, with the moduli of at least wide_min_bits
- * bits (5..30; 30 is the default plan) on the two-limb path.  Head terms with
+ * bits (5..32; 32 is the default plan) on the two-limb paths.  Head terms with
  * modulus 1 (their value is 0) are not in any range.  Writes min(*count, cap)
  * ranges to `out` (caller-owned, may be NULL when cap = 0), sets *count to the
  * number of ranges and *terms (may be NULL) to the number of terms they cover.
  * Needs no GPU.  EINVAL: bad formula, n = 0, P = 0, guard_bits not a positive
- * multiple of 32, W > 1280, wide_min_bits outside 5..30; ERANGE: a modulus
+ * multiple of 32, W > 1280, wide_min_bits outside 5..32; ERANGE: a modulus
  * would reach 2^60. */
 bbp_status bbp_explain(bbp_formula f, uint64_t n, uint32_t P, uint32_t guard_bits, uint32_t wide_min_bits,
                        bbp_range* out, uint32_t cap, uint32_t* count, uint64_t* terms);
@@ -244,9 +249,12 @@ bbp_status bbp_serve_stats(bbp_plan p, bbp_serve_info* info);
 /* Counters of the last compute call on this plan. */
 bbp_status bbp_plan_stats(bbp_plan p, bbp_stats* out);
 
-/* Issue-rate probe of the integer pipes (kind 0: 32-bit multiply-add low half,
- * 1: high half, 2: 32x32->64 wide, 3: 32-bit add).  Runs one CTA of 1024 threads
- * per SM and reports warp-lane operations per SM clock (median over SMs). */
+/* Issue-rate probe of the integer pipes, in 8 independent dependency chains per
+ * thread (kind 0: mad.lo, the low half of a 32x32 product with an addend; 1: mad.hi;
+ * 2: mad.wide, the full product with a 64-bit addend; 3: 32-bit add; 4: mul.hi;
+ * 5: mul.wide without an addend, both halves used; 6: mul.wide followed by a
+ * separate 64-bit add).  Runs one CTA of 1024 threads per SM and reports warp-lane
+ * operations per SM clock (median over SMs).  EINVAL for another kind. */
 bbp_status bbp_imad_probe(bbp_plan p, int kind, double* lanes_per_clk_per_sm);
 
 /* No-allocation partial sum.  The paper has no counterpart: this entry point exists
@@ -267,8 +275,10 @@ bbp_status bbp_imad_probe(bbp_plan p, int kind, double* lanes_per_clk_per_sm);
  * device uses the same array and zeroes it first; calls that overlap on the GPU
  * (other streams or threads) race on it and must be serialized by the caller.
  * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress with that device current); make that first call before
- * any stream capture.
+ * (cudaGetSymbolAddress with that device current) and keeps it for the life of
+ * the process; make that first call before any stream capture, and do not call
+ * this entry point on a device after cudaDeviceReset of that device (the kept
+ * address would belong to the context the reset destroyed).
  * Errors: BBP_EINVAL as bbp_partial_sum, BBP_ERANGE, BBP_ESCRATCH, BBP_ECUDA. */
 bbp_status bbp_partial_sum_noalloc(bbp_formula f, uint32_t denominator, uint64_t k_begin, uint64_t k_end,
                                    uint64_t n, uint32_t P, uint32_t guard_bits, uint32_t* d_out_limbs,

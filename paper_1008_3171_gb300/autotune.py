@@ -7,13 +7,15 @@ Sweeps the launch parameters the C ABI reads from a tune table
 * streams       -- independent pairs of terms per thread (instruction-level parallelism),
 * cta           -- threads per CTA of the single-query head kernel,
 * limb_bump     -- accumulator limb class above the smallest that holds W bits,
-* wide_min_bits -- Montgomery width: moduli of at least this many bits use the
-                   two-limb (64-bit) path, smaller ones the one-limb (32-bit) path,
+* wide_min_bits -- Montgomery width: moduli of at least this many bits use a
+                   two-limb (64-bit) path, smaller ones a one-limb (32-bit) path (lazy
+                   residues below 2^29, fully reduced ones for 30 and 31 bits),
 * grab          -- warp tiles handed out per queue operation in batched passes.
 
 run x streams, then cta, then limb_bump are timed on a slice of the n = 1e12
 query (series 0, 1e9 terms of the 64-bit path); wide_min_bits on the whole
-n = 1e9, P = 128 query (moduli up to 2^30); grab on a seeded calibration batch.
+n = 3e9, P = 128 query (moduli up to 2^31.5, so every crossover moves terms);
+grab on a seeded calibration batch.
 Every setting computes bit-identical results (the sum is exact; the sweep checks
 it), so only time is compared.
 
@@ -36,7 +38,7 @@ RUNS = (16, 32, 64, 128)
 STREAMS = (1, 2)
 CTAS = (64, 128, 256)
 LIMB_BUMPS = (0, 1)
-WIDE_MIN_BITS = (16, 22, 26, 30)
+WIDE_MIN_BITS = (16, 22, 26, 30, 32)
 GRABS = (2, 4, 8, 16, 32)
 
 
@@ -124,11 +126,11 @@ def tune(out_path: str, slice_terms: int = 1_000_000_000, batch: int = 512) -> d
     setting["cta"] = _sweep(bbp, "cta", CTAS, setting, slice_work, measured)
     setting["limb_bump"] = _sweep(bbp, "limb_bump", LIMB_BUMPS, setting, slice_work, measured)
 
-    def n1e9_work(p):
-        v = p.bits(10**9, 128)
+    def n3e9_work(p):
+        v = p.bits(3 * 10**9, 128)
         return v, p.stats()["terms"]
 
-    setting["wide_min_bits"] = _sweep(bbp, "wide_min_bits", WIDE_MIN_BITS, setting, n1e9_work, measured, reps=5)
+    setting["wide_min_bits"] = _sweep(bbp, "wide_min_bits", WIDE_MIN_BITS, setting, n3e9_work, measured, reps=5)
     ns, Ps = workloads.batched_queries(count=batch, seed=3, lo=4.0, hi=8.5)
 
     def batch_work(p):

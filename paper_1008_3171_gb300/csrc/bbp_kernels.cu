@@ -160,6 +160,21 @@ __global__ void imad_probe_kernel(int iters, unsigned long long* cycles, uint32_
         if (KIND == 1) asm volatile("mad.hi.u32 %0, %0, %1, %2;" : "+r"(a[j]) : "r"(b), "r"(c));
         if (KIND == 2) asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(w[j]) : "r"(static_cast<uint32_t>(w[j])), "r"(b));
         if (KIND == 3) asm volatile("add.u32 %0, %0, %1;" : "+r"(a[j]) : "r"(b));
+        if (KIND == 4) asm volatile("mul.hi.u32 %0, %0, %1;" : "+r"(a[j]) : "r"(b));
+        if (KIND == 5) {  // full product without an addend; both halves feed the next operand
+          asm volatile("{\n\t.reg .u32 l, h, s;\n\t"
+                       "mov.b64        {l, h}, %0;\n\t"
+                       "add.u32        s, l, h;\n\t"
+                       "mul.wide.u32   %0, s, %1;\n\t}"
+                       : "+l"(w[j]) : "r"(b));
+        }
+        if (KIND == 6) {  // full product, its 64-bit addend applied by a separate add
+          asm volatile("{\n\t.reg .u32 l, h;\n\t.reg .u64 p;\n\t"
+                       "mov.b64        {l, h}, %0;\n\t"
+                       "mul.wide.u32   p, l, %1;\n\t"
+                       "add.u64        %0, %0, p;\n\t}"
+                       : "+l"(w[j]) : "r"(b));
+        }
       }
     }
   }
@@ -277,6 +292,9 @@ cudaError_t launch_imad_probe(int kind, int blocks, int threads, int iters, unsi
     case 1: imad_probe_kernel<1><<<blocks, threads, 0, s>>>(iters, cycles_out, smid_out, sink); break;
     case 2: imad_probe_kernel<2><<<blocks, threads, 0, s>>>(iters, cycles_out, smid_out, sink); break;
     case 3: imad_probe_kernel<3><<<blocks, threads, 0, s>>>(iters, cycles_out, smid_out, sink); break;
+    case 4: imad_probe_kernel<4><<<blocks, threads, 0, s>>>(iters, cycles_out, smid_out, sink); break;
+    case 5: imad_probe_kernel<5><<<blocks, threads, 0, s>>>(iters, cycles_out, smid_out, sink); break;
+    case 6: imad_probe_kernel<6><<<blocks, threads, 0, s>>>(iters, cycles_out, smid_out, sink); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

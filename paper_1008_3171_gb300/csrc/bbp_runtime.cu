@@ -421,7 +421,7 @@ bbp_status bbp_bits(bbp_plan p, uint64_t n, uint32_t P, uint8_t* out, uint32_t* 
 }
 
 bbp_status bbp_imad_probe(bbp_plan p, int kind, double* lanes_per_clk_per_sm) {
-  if (!p || !lanes_per_clk_per_sm || kind < 0 || kind > 3) return BBP_EINVAL;
+  if (!p || !lanes_per_clk_per_sm || kind < 0 || kind > 6) return BBP_EINVAL;
   BBP_CUDA(cudaSetDevice(p->device));
   const int blocks = p->sm_count;
   const int threads = 1024;

@@ -1,6 +1,6 @@
 // Autotune table loading: a small JSON object written by the autotuner
 // (paper_1008_3171_gb300/autotune.py), e.g. {"run": 32, "streams": 1, "grab": 8,
-// "cta": 256, "limb_bump": 0, "wide_min_bits": 30}.  Unknown keys are ignored;
+// "cta": 256, "limb_bump": 0, "wide_min_bits": 32}.  Unknown keys are ignored;
 // missing or out-of-range values keep the built-in defaults.
 #include <cstdio>
 #include <cstdlib>
