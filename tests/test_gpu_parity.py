@@ -271,3 +271,14 @@ def test_every_limb_class_matches_oracle(plan64, P):
         kb = 31 * 10**9 + 17
         got = plan64.partial_sum(0, j, kb, kb + 40_001, 10**12, P)
         assert got == oracle.c_partial_sum(0, j, kb, kb + 40_001, 10**12, P, 64), (P, j)
+
+
+def test_imad_probe_kinds(bbp, plan64):
+    """Every probe kind reports a positive issue rate, a full 32-bit product at most
+    as fast as its low half; an unknown kind is refused."""
+    rates = [plan64.imad_probe(k) for k in range(7)]
+    assert all(r > 0 for r in rates)
+    assert rates[5] <= rates[0] * 1.05 and rates[2] <= rates[0] * 1.05
+    with pytest.raises(bbp.BBPError) as e:
+        plan64.imad_probe(7)
+    assert e.value.status == bbp.BBP_EINVAL
