@@ -155,21 +155,22 @@ def test_partial_sums_full_size_sampled(plan64, n):
         assert ne > he
 
 
+@pytest.mark.parametrize("formula", [0, 1])
 @pytest.mark.parametrize("bits", [29, 30, 31, 32, 46, 47])
-def test_modulus_path_boundaries(plan64, bits):
+def test_modulus_path_boundaries(plan64, bits, formula):
     """k-ranges whose moduli cross 2^bits, on every series: the one-limb lazy and
     reduced paths meet at 2^29 (bitlen 30), the reduced one-limb path and the
     three-word two-limb path at 2^31 (bitlen 32), the three- and four-word two-limb
     paths at 2^46 (bitlen 47); 2^30 and 2^32 cross inside a path.  n = 2e15 - 3
-    reaches all of them in the head."""
+    reaches all of them in the head, for Eq. 2 and Eq. 1."""
     n, P, G = 2 * 10**15 - 3, 256, 64
-    f = o1.BELLARD
+    f = o1.FORMULAS[formula]
     for j, s in enumerate(f.series):
         k_cross = ((1 << (bits - 1)) - s.b) // s.a
         for kb, cnt in ((max(1, k_cross - 1500), 3001), (max(1, k_cross - 70_000), 140_001)):
-            got = plan64.partial_sum(0, j, kb, kb + cnt, n, P)
-            want = oracle.c_partial_sum(0, j, kb, kb + cnt, n, P, G)
-            assert got == want, (bits, j, kb, cnt)
+            got = plan64.partial_sum(formula, j, kb, kb + cnt, n, P)
+            want = oracle.c_partial_sum(formula, j, kb, kb + cnt, n, P, G)
+            assert got == want, (formula, bits, j, kb, cnt)
 
 
 def test_raw_accumulator_matches_oracle(bbp, plan32, plan64):
