@@ -3,7 +3,9 @@
 // Every query of a batch is planned into jobs (bbp_planner.cpp): head jobs -- one
 // range of head terms of one series, with the ladder parameters of its moduli --
 // and tail jobs.  Queries are sorted by size and cut into waves whose work grows
-// geometrically (the smallest queries first); a wave is one tail launch plus one
+// geometrically (the smallest queries first) up to 1/12 of the batch, so the
+// largest queries finish over the last several waves rather than together at the
+// end of one; a wave is one tail launch plus one
 // persistent launch per kernel variant (limb capacity x modulus path) in which
 // warps take `grab` tiles of the current job at a time (queue_kernel), so queries
 // of very different sizes share the GPU at tile granularity and small ones finish
@@ -135,7 +137,7 @@ void release_batch_state(bbp_plan p) {
   p->batch = nullptr;
 }
 
-constexpr int kMaxWaves = 16;
+constexpr int kMaxWaves = 24;
 
 // Plans `count` queries into the batch's pinned staging buffers.
 struct BatchPlan {
@@ -238,7 +240,7 @@ static bbp_status plan_batch(bbp_plan p, int f, uint32_t count, const uint64_t* 
     Q.L = L;
     Q.out_offset = q * kOutStride;
   }
-  // waves: queries by size, each wave at least twice the work of the ones before it
+  // waves: queries by size, each wave twice the work of the ones before it, at most 1/12 of the total
   std::vector<uint32_t> qorder(count);
   std::iota(qorder.begin(), qorder.end(), 0u);
   std::stable_sort(qorder.begin(), qorder.end(), [&](uint32_t x, uint32_t y) { return qterms[x] < qterms[y]; });
@@ -247,13 +249,14 @@ static bbp_status plan_batch(bbp_plan p, int f, uint32_t count, const uint64_t* 
     uint64_t total = 0;
     for (uint64_t t : qterms) total += t;
     const uint64_t first = std::max<uint64_t>(total / 4096, 1);  // the first wave: 1/4096 of the work
+    const uint64_t step_cap = std::max<uint64_t>(total / 12, 1);  // no wave beyond 1/12 of the work
     uint64_t done = 0, target = first;
     uint32_t w = 0;
     for (uint32_t i = 0; i < count; ++i) {
       const uint32_t q = qorder[i];
       if (done >= target && w + 1 < static_cast<uint32_t>(kMaxWaves)) {
         ++w;
-        target = std::max(target, done) * 2;
+        target = std::min(std::max(target, done) * 2, done + step_cap);
       }
       wave_of[q] = w;
       done += qterms[q];
