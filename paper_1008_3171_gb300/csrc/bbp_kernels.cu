@@ -75,6 +75,20 @@ __global__ void tail_kernel(const TailArgs A) {
     if (t[i]) atomicAdd(A.slots + i, static_cast<unsigned long long>(t[i]));
 }
 
+// The tail ranges of several series in one launch: thread i takes the i-th term of
+// the ranges laid end to end.
+__global__ void tail_set_kernel(const TailSet S) {
+  uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  uint32_t r = 0;
+  while (r < S.n && i >= S.a[r].count) i -= S.a[r++].count;
+  if (r >= S.n) return;
+  const TailArgs& A = S.a[r];
+  uint32_t t[kMaxLimbs];
+  tail_term(A, A.k_begin + i, t);
+  for (uint32_t l = 0; l < A.L; ++l)
+    if (t[l]) atomicAdd(A.slots + l, static_cast<unsigned long long>(t[l]));
+}
+
 // ---------------------------------------------------------------- fold / finalize
 
 __global__ void zero_slots_kernel(unsigned long long* slots, int L) {
@@ -266,6 +280,15 @@ cudaError_t launch_tail(const TailArgs& a, cudaStream_t s) {
   const int threads = 128;
   const int blocks = static_cast<int>((a.count + threads - 1) / threads);
   tail_kernel<<<blocks, threads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tail_set(const TailSet& set, cudaStream_t s) {
+  uint64_t total = 0;
+  for (uint32_t r = 0; r < set.n; ++r) total += set.a[r].count;
+  if (total == 0) return cudaSuccess;
+  const int threads = 128;
+  tail_set_kernel<<<static_cast<unsigned>((total + threads - 1) / threads), threads, 0, s>>>(set);
   return cudaGetLastError();
 }
 

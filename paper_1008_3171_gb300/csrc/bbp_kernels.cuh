@@ -40,6 +40,14 @@ struct TailArgs {
   unsigned long long* slots;
 };
 
+// The tail ranges of up to kMaxTailSet series, launched together (tail terms are
+// few: about W / step per series).
+constexpr int kMaxTailSet = 7;
+struct TailSet {
+  TailArgs a[kMaxTailSet];
+  uint32_t n;  // ranges in use
+};
+
 constexpr int kMaxLimbs = 40;    // W <= 1280 bits
 constexpr int kHeadThreads = 256;
 // Compiled accumulator capacities (limbs per thread) of the head and queue
@@ -91,6 +99,7 @@ struct BatchDev {
 cudaError_t launch_head(const HeadArgs& a, int path, int streams, int lmax, int blocks, cudaStream_t s,
                         int threads = kHeadThreads);
 cudaError_t launch_tail(const TailArgs& a, cudaStream_t s);
+cudaError_t launch_tail_set(const TailSet& set, cudaStream_t s);
 cudaError_t launch_zero_slots(unsigned long long* slots, int L, cudaStream_t s);
 cudaError_t launch_fold_limbs(const unsigned long long* slots, int L, uint32_t* out_limbs, cudaStream_t s);
 cudaError_t launch_finalize_bits(const unsigned long long* slots, int L, uint32_t P, uint64_t bound,

@@ -177,11 +177,13 @@ bbp_status launch_ranges(bbp_plan p, int f, uint64_t n, uint32_t W, const std::v
   const int lmax = pick_lmax(W, p->limb_bump);
   if (lmax == 0) return BBP_EINVAL;
   float total_ms = 0;
+  TailSet tails{};
   for (const TermRange& r : ranges) {
     const SeriesDef& s = F.s[r.j];
     const bool odd_start = F.alternating && (r.k_begin & 1ull);
-    if (r.tail) {
-      TailArgs a{};
+    if (r.tail) {  // collected, and launched together once the set is full or the ranges end
+      TailArgs& a = tails.a[tails.n++];
+      a = TailArgs{};
       a.d = n - 1;
       a.k_begin = r.k_begin;
       a.count = r.count;
@@ -194,9 +196,12 @@ bbp_status launch_ranges(bbp_plan p, int f, uint64_t n, uint32_t W, const std::v
       a.alternating = F.alternating;
       a.negate = s.sign < 0 ? 1u : 0u;
       a.slots = slots;
-      BBP_CUDA(launch_tail(a, st));
-      p->stats.kernel_launches++;
       p->stats.terms += r.count;
+      if (tails.n == kMaxTailSet) {
+        BBP_CUDA(launch_tail_set(tails, st));
+        p->stats.kernel_launches++;
+        tails.n = 0;
+      }
       continue;
     }
     HeadArgs a{};
@@ -211,15 +216,20 @@ bbp_status launch_ranges(bbp_plan p, int f, uint64_t n, uint32_t W, const std::v
     a.L = L;
     a.alternating = F.alternating;
     a.negate = ((s.sign < 0) != odd_start) ? 1u : 0u;
-    a.run = static_cast<uint32_t>(p->run);
     a.window = r.window;
     a.first = r.first;
     a.slots = slots;
     const int streams = head_streams(p, r.path);
-    const uint64_t tile = tile_terms(p, r.path);
-    const uint64_t ntiles = (r.count + tile - 1) / tile;
     const int warps_per_block = p->cta / 32;
     const int occ = head_occupancy(r.path, streams, lmax, p->cta);
+    const uint64_t resident_warps = static_cast<uint64_t>(occ) * p->sm_count * warps_per_block;
+    // a short range takes fewer consecutive terms per stream, so that its tiles
+    // spread over the GPU's resident warps instead of a few warps running long runs
+    uint32_t run = static_cast<uint32_t>(p->run);
+    auto tiles_for = [&](uint32_t rn) { return (r.count + 32ull * streams * rn - 1) / (32ull * streams * rn); };
+    while (run % 4 == 0 && tiles_for(run) < resident_warps) run /= 2;
+    a.run = run;
+    const uint64_t ntiles = tiles_for(run);
     const uint64_t want = (ntiles + warps_per_block - 1) / warps_per_block;
     const int blocks = static_cast<int>(std::max<uint64_t>(1, std::min<uint64_t>(want, uint64_t(occ) * p->sm_count)));
     if (p->profile) BBP_CUDA(cudaEventRecord(p->ev0, st));
@@ -236,6 +246,10 @@ bbp_status launch_ranges(bbp_plan p, int f, uint64_t n, uint32_t W, const std::v
     p->stats.terms += r.count;
     p->stats.head_terms += r.count;
     p->stats.imad_model += r.imad;
+  }
+  if (tails.n > 0) {
+    BBP_CUDA(launch_tail_set(tails, st));
+    p->stats.kernel_launches++;
   }
   p->stats.head_ms += total_ms;
   return BBP_OK;
