@@ -104,8 +104,8 @@ def host_cores() -> int:
     return os.cpu_count() or 1
 
 
-def survey_imad_model(bbp, n: int, P: int, G: int) -> float:
-    """Multiply instructions of the query's head terms by the survey's per-term model:
+def per_term_imad_model(bbp, n: int, P: int, G: int) -> float:
+    """Multiply instructions of the query's head terms by a per-term work model:
     16 ceil(log2 e) + 4 L + 50 for a two-limb (64-bit) modulus, 5 ceil(log2 e) + 3 L + 25
     for a one-limb modulus (below 2^31), L = W/32 limbs, e the term's exponent; summed
     exactly over the query's exponents (counted per bit length), host-only."""
@@ -400,8 +400,8 @@ def run_gpu(args):
     max_mhz = (clocks or {}).get("sm_max_mhz") or SM_MAX_MHZ_FALLBACK
     peak = sms * IMAD_LANES_PER_CLK_PER_SM * max_mhz * 1e6 / 1e12        # T multiply instructions / s
     achieved = (imad / (head_ms / 1e3)) / 1e12 if head_ms > 0 else None
-    survey = survey_imad_model(bbp, N_POS, P_BITS, GUARD) * args.steps / max(1, world)
-    achieved_survey = (survey / (head_ms / 1e3)) / 1e12 if head_ms > 0 else None
+    modelled = per_term_imad_model(bbp, N_POS, P_BITS, GUARD) * args.steps / max(1, world)
+    achieved_model = (modelled / (head_ms / 1e3)) / 1e12 if head_ms > 0 else None
     value = terms / t_dev
     e2e_value = terms / t_e2e
     ncu = head_kernel_ncu()
@@ -439,10 +439,10 @@ def run_gpu(args):
                 "d2h_bytes_per_step": nbytes + 4,
                 "note": "bbp_bits with host output; the query (n, P) travels as kernel arguments"},
         "gpu_launches": launches,
-        "roofline": {"bound": "alu", "achieved": achieved_survey, "peak": peak, "unit": "T IMAD/s",
-                     "frac": (achieved_survey / peak) if achieved_survey else None,
+        "roofline": {"bound": "alu", "achieved": achieved_model, "peak": peak, "unit": "T IMAD/s",
+                     "frac": (achieved_model / peak) if achieved_model else None,
                      "traffic": ncu.get("dram_bytes_per_launch"),
-                     "model": "survey: 16 ceil(log2 e) + 4L + 50 IMAD per two-limb term, 5 ceil(log2 e) + 3L + 25 "
+                     "model": "per term: 16 ceil(log2 e) + 4L + 50 IMAD per two-limb term, 5 ceil(log2 e) + 3L + 25 "
                               "per one-limb term, summed over the query's exponents",
                      "achieved_half_products": achieved,
                      "frac_half_products": (achieved / peak) if achieved else None,
