@@ -283,3 +283,18 @@ def test_imad_probe_kinds(bbp, plan64):
     with pytest.raises(bbp.BBPError) as e:
         plan64.imad_probe(7)
     assert e.value.status == bbp.BBP_EINVAL
+
+
+@pytest.mark.parametrize("P", [64, 1000])
+@pytest.mark.parametrize("bits", [30, 32, 47])
+def test_modulus_path_boundaries_small_and_large_accumulators(plan64, bits, P):
+    """The path crossings (one-limb lazy/reduced, one-/two-limb, three-/four-word) with
+    the smallest and the largest accumulator classes (4 and 40 limbs)."""
+    n, G = 2 * 10**15 - 3, 64
+    f = o1.BELLARD
+    for j in (0, 5):
+        s = f.series[j]
+        kb = max(1, ((1 << (bits - 1)) - s.b) // s.a - 20_000)
+        got = plan64.partial_sum(0, j, kb, kb + 40_001, n, P)
+        want = oracle.c_partial_sum(0, j, kb, kb + 40_001, n, P, G)
+        assert got == want, (bits, P, j)
