@@ -205,10 +205,10 @@ bbp_status bbp_finalize_async(bbp_plan p, bbp_formula f, uint64_t n, uint32_t P,
  * MSB first.  valid_bits[count] (may be NULL): certified bits.  latency_ms[count]
  * (may be NULL): device time from the start of the pass to each query's finalize.
  * Blocks until done.  EINVAL: a bad query, a too-small out_stride or count > 2^24.  ERANGE: a
- * modulus would reach 2^60, or a query needs 2^32 - 2^24 or more warp tiles (more
- * than about 8.8e12 head terms at the default 2048-term tile, n above about
- * 1.2e13), past which its 64-bit carry-save limbs could overflow; run such a
- * query with bbp_bits or bbp_accumulate_async. */
+ * modulus would reach 2^60, or a query needs 2^32 - 2^24 or more warp tiles (at the
+ * default settings a tile is 4096 terms on moduli of 32 to 46 bits and 2048 terms
+ * elsewhere: n above about 2.4e13), past which its 64-bit carry-save limbs could
+ * overflow; run such a query with bbp_bits or bbp_accumulate_async. */
 bbp_status bbp_bits_batch(bbp_plan p, bbp_formula f, uint32_t count, const uint64_t* n, const uint32_t* P,
                           uint8_t* out, uint32_t out_stride, uint32_t* valid_bits, double* latency_ms);
 
