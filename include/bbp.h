@@ -155,7 +155,8 @@ typedef struct bbp_range {
                             three-word square, m < 2^46; 2 two limbs, four-word square, m < 2^60 */
   uint32_t window;       /* head: ladder window bits (a window's multiplication is a shift) */
   uint32_t first;        /* head: bits taken by the first window (no squaring) */
-  uint32_t reserved;
+  uint32_t first_max;    /* head: largest first-window value the range's moduli allow; a warp whose
+                            exponents' top first + 1 bits stay within it takes that bit too */
   uint64_t k_begin;      /* first k */
   uint64_t count;        /* number of terms */
   double imad;           /* modelled 32-bit multiply halves of the range (head only; see bbp_stats) */

@@ -73,7 +73,7 @@ class bbp_range(ctypes.Structure):
         ("path", ctypes.c_uint32),
         ("window", ctypes.c_uint32),
         ("first", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32),
+        ("first_max", ctypes.c_uint32),
         ("k_begin", ctypes.c_uint64),
         ("count", ctypes.c_uint64),
         ("imad", ctypes.c_double),
@@ -256,7 +256,7 @@ def bbp_explain(formula: int, n: int, P: int, guard_bits: int = 64, wide_min_bit
     buf = (bbp_range * max(count.value, 1))()
     _check(_lib.bbp_explain(formula, n, P, guard_bits, wide_min_bits, buf, count.value, ctypes.byref(count),
                             ctypes.byref(terms)), "bbp_explain")
-    names = [f for f, _ in bbp_range._fields_ if f != "reserved"]
+    names = [f for f, _ in bbp_range._fields_]
     return [{f: getattr(buf[i], f) for f in names} for i in range(count.value)], terms.value
 
 

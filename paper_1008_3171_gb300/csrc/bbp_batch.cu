@@ -215,6 +215,7 @@ static bbp_status plan_batch(bbp_plan p, int f, uint32_t count, const uint64_t* 
         a.run = static_cast<uint32_t>(p->run);
         a.window = r.window;
         a.first = r.first;
+        a.first_max = r.first_max;
         a.slots = slots;
         const int v = lmax_index(lmax) * kNumPaths + r.path;
         vj[v].push_back(a);

@@ -22,6 +22,8 @@ struct HeadArgs {
   uint32_t run;          // consecutive terms per stream (even)
   uint32_t window;       // ladder window bits (>= 1)
   uint32_t first;        // bits taken by the first window (0 allowed)
+  uint32_t first_max;    // largest first-window value the moduli allow (>= 2^first - 1); a warp
+                         // whose top first + 1 exponent bits stay within it takes one more bit
   unsigned long long* slots;  // L carry-save accumulators, limb i at slots[i]
 };
 

@@ -110,8 +110,8 @@ extern "C" bbp_status bbp_partial_sum_noalloc(bbp_formula f, uint32_t denominato
       const int lbits = bitlen(static_cast<uint64_t>(s.a) * (ke - 1) + s.b);
       const int path = path_for_bits(lbits);
       const int streams = path == 1 ? 2 : 1;
-      uint8_t window, first;
-      window_params(path, lbits, &window, &first);
+      uint8_t window, first, first_max;
+      window_params(path, lbits, &window, &first, &first_max);
       HeadArgs a{};
       a.d = d;
       a.k_begin = kb;
@@ -127,6 +127,7 @@ extern "C" bbp_status bbp_partial_sum_noalloc(bbp_formula f, uint32_t denominato
       a.run = kRun;
       a.window = window;
       a.first = first;
+      a.first_max = first_max;
       a.slots = slots;
       const uint64_t tile = 32ull * static_cast<uint64_t>(streams) * kRun;
       const uint64_t ntiles = (a.count + tile - 1) / tile;

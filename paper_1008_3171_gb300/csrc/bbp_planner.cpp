@@ -64,23 +64,27 @@ uint64_t natural_end(const FormulaDef& f, uint32_t j, uint64_t d, uint32_t W) {
   }
 }
 
-void window_params(int path, int lbits, uint8_t* window, uint8_t* first) {
+void window_params(int path, int lbits, uint8_t* window, uint8_t* first, uint8_t* first_max) {
   // A squaring with a window shift s keeps its result below 2m while
   //   path 0 (one word, lazy x < 2m):      lbits + s <= 30
   //   path 3 (one word, reduced x < m):    lbits + s <= 32
   //   paths 1, 2 (two words, lazy x < 2m): lbits + s <= 61
   // and s <= 2^window - 1.  The first window starts from x = (R mod m) << w0 < m 2^w0,
-  // w0 <= 2^first - 1, and the squaring after it (general routine on paths 1 and 2,
-  // shift at most one bit) needs lbits + 2 w0 + 1 <= 32 (one word) / 64 (two words).
+  // and the squaring after it (general routine on paths 1 and 2, shift at most one
+  // bit) needs lbits + 2 w0 + 1 <= 32 (one word) / 64 (two words): w0 <= first_max.
+  // `first` is the most bits whose every value fits (2^first - 1 <= first_max); the
+  // kernel takes one bit more where the exponents' top bits happen to fit.
   const bool wide = path == 1 || path == 2;
   const int shift_cap = path == 0 ? 30 - lbits : path == 3 ? 32 - lbits : 61 - lbits;
   const int rbits = wide ? 64 : 32;
   int w = 0;
   while (w < 4 && (1 << (w + 1)) - 1 <= shift_cap) ++w;
+  const int w0_max = std::max(0, (rbits - 1 - lbits) / 2);  // lbits + 2 w0 + 1 <= rbits
   int h = 0;
-  while (h < 4 && lbits + 2 * ((1 << (h + 1)) - 1) + 1 <= rbits) ++h;
+  while (h < 4 && (1 << (h + 1)) - 1 <= w0_max) ++h;
   *window = static_cast<uint8_t>(w);
   *first = static_cast<uint8_t>(h);
+  *first_max = static_cast<uint8_t>(w0_max);
 }
 
 int path_for_bits(int lbits, int wide_min_bits) {
@@ -115,14 +119,25 @@ double range_imad(const FormulaDef& f, const SeriesDef& s, uint64_t d, uint32_t 
   const int64_t v0 = static_cast<int64_t>(d) + s.c + static_cast<int64_t>(W) - rb;  // v at k = 0
   const int64_t k_lo = static_cast<int64_t>(r.k_begin);
   const int64_t k_hi = static_cast<int64_t>(r.k_begin + r.count) - 1;
+  // terms with lo_v <= v0 - step k <= hi_v
+  auto terms = [&](int64_t lo_v, int64_t hi_v) -> double {
+    const int64_t ka = std::max(k_lo, ceil_div(v0 - hi_v, f.step));
+    const int64_t kb = std::min(k_hi, floor_div(v0 - lo_v, f.step));
+    return kb >= ka ? static_cast<double>(kb - ka + 1) : 0.0;
+  };
   double total = 0;
   for (int i = 0; i < 64; ++i) {
     const int64_t lo_v = i == 0 ? 0 : (int64_t{1} << (i - 1));
     const int64_t hi_v = i == 0 ? 0 : (i == 63 ? std::numeric_limits<int64_t>::max() : (int64_t{1} << i) - 1);
-    // lo_v <= v0 - step k <= hi_v
-    const int64_t ka = std::max(k_lo, ceil_div(v0 - hi_v, f.step));
-    const int64_t kb = std::min(k_hi, floor_div(v0 - lo_v, f.step));
-    if (kb >= ka) total += static_cast<double>(kb - ka + 1) * head_term_imad(r.path, i, r.first, lmax);
+    if (i >= r.first + 2 && i < 63) {
+      // exponents whose top first + 1 bits are at most first_max take one more
+      // first-window bit, so one squaring fewer
+      const int64_t t = static_cast<int64_t>(r.first_max + 1) << (i - r.first - 1);
+      total += terms(lo_v, t - 1) * head_term_imad(r.path, i, r.first + 1, lmax);
+      total += terms(t, hi_v) * head_term_imad(r.path, i, r.first, lmax);
+    } else {
+      total += terms(lo_v, hi_v) * head_term_imad(r.path, i, r.first, lmax);
+    }
   }
   return total;
 }
@@ -153,8 +168,8 @@ int plan_series(const FormulaDef& f, uint32_t j, uint64_t n, uint32_t W, uint32_
       uint64_t k1 = std::min(head_hi, first_k_at_least(1ull << l, s.a, s.b));
       if (k0 >= k1) continue;
       const int path = path_for_bits(l, wide_min_bits);
-      uint8_t w, h;
-      window_params(path, l, &w, &h);
+      uint8_t w, h, fm;
+      window_params(path, l, &w, &h, &fm);
       if (!groups.empty() && groups.back().path == path && groups.back().w == w && groups.back().h == h &&
           groups.back().k1 == k0) {
         groups.back().k1 = k1;
@@ -185,12 +200,15 @@ int plan_series(const FormulaDef& f, uint32_t j, uint64_t n, uint32_t W, uint32_
       }
     }
     for (const Group& g : merged) {
+      uint8_t w, h, fm;
+      window_params(g.path, g.lmax_bits, &w, &h, &fm);  // the group's largest moduli bound w0
       TermRange r{};
       r.j = j;
       r.tail = 0;
       r.path = static_cast<uint8_t>(g.path);
       r.window = g.w;
       r.first = g.h;
+      r.first_max = fm;
       r.k_begin = g.k0;
       r.count = g.k1 - g.k0;
       r.imad = range_imad(f, s, d, W, r, static_cast<int>(lmax));

@@ -48,6 +48,7 @@ struct TermRange {
                       //       3 one word, reduced residues (30, 31)
   uint8_t window;     // head: ladder window bits
   uint8_t first;      // head: first-window bits
+  uint8_t first_max;  // head: largest first-window value the range's moduli allow
   uint64_t k_begin;   // first k
   uint64_t count;     // number of terms
   double imad;        // modelled multiply instructions for the range (head only)
@@ -69,8 +70,11 @@ uint64_t natural_end(const FormulaDef& f, uint32_t j, uint64_t d, uint32_t W);
 // paths) but not raised.
 int path_for_bits(int lbits, int wide_min_bits = kWideMinBits);
 
-// Ladder parameters for moduli of at most `lbits` bits on the given path.
-void window_params(int path, int lbits, uint8_t* window, uint8_t* first);
+// Ladder parameters for moduli of at most `lbits` bits on the given path: the
+// window bits, the first-window bits, and the largest first-window value w0 the
+// first squaring allows (x = (R mod m) << w0 < m 2^w0 needs lbits + 2 w0 + 1 <= R's
+// width); first_max >= 2^first - 1.
+void window_params(int path, int lbits, uint8_t* window, uint8_t* first, uint8_t* first_max);
 
 // Algorithmic work of one head term whose ladder exponent has nb bits, counted as
 // 32-bit halves of 32x32-bit products (the low or high word of a product; a full

@@ -218,6 +218,7 @@ bbp_status launch_ranges(bbp_plan p, int f, uint64_t n, uint32_t W, const std::v
     a.negate = ((s.sign < 0) != odd_start) ? 1u : 0u;
     a.window = r.window;
     a.first = r.first;
+    a.first_max = r.first_max;
     a.slots = slots;
     const int streams = head_streams(p, r.path);
     const int warps_per_block = p->cta / 32;
@@ -368,7 +369,7 @@ bbp_status bbp_explain(bbp_formula f, uint64_t n, uint32_t P, uint32_t guard_bit
       o.path = r.path;
       o.window = r.window;
       o.first = r.first;
-      o.reserved = 0;
+      o.first_max = r.first_max;
       o.k_begin = r.k_begin;
       o.count = r.count;
       o.imad = r.imad;

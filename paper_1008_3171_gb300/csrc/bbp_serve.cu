@@ -218,6 +218,7 @@ bbp_status plan_query_work(bbp_plan p, uint64_t n, uint32_t P, Query* q) {
       a.run = static_cast<uint32_t>(p->run);
       a.window = r.window;
       a.first = r.first;
+      a.first_max = r.first_max;
       w.tile = tile_terms(p, r.path);
       w.tiles = (r.count + w.tile - 1) / w.tile;
       w.variant = lmax_index(lmax) * kNumPaths + r.path;

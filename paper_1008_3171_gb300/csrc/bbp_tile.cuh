@@ -163,7 +163,15 @@ __device__ __forceinline__ void process_tile(const HeadArgs& A, const uint64_t t
       }
     }
     const int nb = static_cast<int>(__reduce_max_sync(0xffffffffu, static_cast<uint32_t>(nbl)));
-    const int h = nb > 0 ? min(static_cast<int>(A.first), nb - 1) : 0;
+    int h = nb > 0 ? min(static_cast<int>(A.first), nb - 1) : 0;
+    if (h + 1 <= nb - 1) {
+      // one more first-window bit (one squaring fewer) when the warp's top h + 1
+      // exponent bits all stay within the first-window bound of the moduli
+      uint32_t top = 0;
+#pragma unroll
+      for (int t = 0; t < NT; ++t) top = max(top, static_cast<uint32_t>(v[t] >> (nb - h - 1)));
+      if (__reduce_max_sync(0xffffffffu, top) <= A.first_max) ++h;
+    }
     const int low = nb - h;  // bits left after the first window
     uint64_t rem[NT];
 #pragma unroll
@@ -179,11 +187,16 @@ __device__ __forceinline__ void process_tile(const HeadArgs& A, const uint64_t t
       }
       rem[t] = low > 0 ? (v[t] & ((1ull << low) - 1ull)) : 0ull;
     }
-    // remaining bits, top down, in groups of `window` bits aligned from the top
+    // remaining bits, top down, in groups of at most `window` bits.  Any split of the
+    // bits into consecutive groups gives the same power.  Path 1 always has 4-bit
+    // windows (its moduli are below 2^47); there the groups are aligned from the
+    // bottom, so only the first one is short and the rest run as a fixed
+    // four-squaring body.  The other paths align them from the top.
     int p = low;
+    const bool w4 = PATH == 1 && window == 4;
     if (PATH == 1 && p > 0) {
       // the first group, with its first squaring on the general routine
-      const int len = min(window, p);
+      const int len = w4 ? ((p - 1) & 3) + 1 : min(window, p);
       p -= len;
       uint32_t sh[NT];
       const uint32_t zero[NT] = {};
@@ -194,6 +207,19 @@ __device__ __forceinline__ void process_tile(const HeadArgs& A, const uint64_t t
       } else {
         square_all_general<NT>(x0, x1, m0, m1, mp, zero, false);
         square_group<PATH, NT>(len - 1, x0, x1, m0, m1, mp, sh);
+      }
+    }
+    if (w4) {
+      const uint32_t zero[NT] = {};
+      while (p > 0) {
+        p -= 4;
+        uint32_t sh[NT];
+#pragma unroll
+        for (int t = 0; t < NT; ++t) sh[t] = static_cast<uint32_t>(rem[t] >> p) & 15u;
+        square_all<PATH, NT>(x0, x1, m0, m1, mp, zero, false);
+        square_all<PATH, NT>(x0, x1, m0, m1, mp, zero, false);
+        square_all<PATH, NT>(x0, x1, m0, m1, mp, zero, false);
+        square_all<PATH, NT>(x0, x1, m0, m1, mp, sh, true);
       }
     }
     while (p > 0) {

@@ -9,7 +9,8 @@ themselves.  It restates, word by word, what the device code does for one term
   * R mod m by bit-serial division, carried to k + 1 with R = q (m + a) + (r - a q);
   * the left-to-right ladder: a first window taken as (R mod m) << w0, then
     groups of `window` bits, each len - 1 plain Montgomery squarings and one
-    squaring with the group's bits shifted in;
+    squaring with the group's bits shifted in (aligned from the top, except on
+    path 1 with 4-bit windows, where they are aligned from the bottom);
   * path 2 (and the first squaring of path 1): the square on four words, the
     shift by funnel shifts, two word-by-word REDC steps with the vanishing low
     word's carry taken as (word != 0) and u m1 accumulated by the multiply;
@@ -227,8 +228,10 @@ def sqr_shift_redc32(x, s, m, mp, do_shift, reduced):
     return r
 
 
-def ladder_term(path, window, first, m, E, W, extra, r_mod_m, valid=True):
-    """2^E mod m by the kernel's ladder, then the W-bit quotient digits."""
+def ladder_term(path, window, first, m, E, W, extra, r_mod_m, valid=True, first_max=0, take_extra=False):
+    """2^E mod m by the kernel's ladder, then the W-bit quotient digits.  take_extra:
+    the warp's top first + 1 exponent bits fit first_max, so the first window takes
+    one more bit (taken here whenever this term's own bits allow it)."""
     wide = path in (1, 2)
     rb = 64 if wide else 32
     mp = neg_inverse32(m & M32)
@@ -236,6 +239,8 @@ def ladder_term(path, window, first, m, E, W, extra, r_mod_m, valid=True):
     assert v >= 0
     nb = v.bit_length() + extra              # the warp's longest exponent
     h = min(first, nb - 1) if nb > 0 else 0
+    if take_extra and h + 1 <= nb - 1 and (v >> (nb - h - 1)) <= first_max:
+        h += 1
     low = nb - h
     w0 = (v >> low) if h > 0 else 0
     x = r_mod_m << w0
@@ -250,8 +255,9 @@ def ladder_term(path, window, first, m, E, W, extra, r_mod_m, valid=True):
         return sqr_shift_redc32(x, sh, m, mp, shifted, path == 3)
 
     p = low
+    w4 = path == 1 and window == 4           # path 1: groups aligned from the bottom, the first one short
     if path == 1 and p > 0:                  # first group: its first squaring on the general routine
-        ln = min(window, p)
+        ln = (p - 1) % 4 + 1 if w4 else min(window, p)
         p -= ln
         sh = (rem >> p) & ((1 << ln) - 1)
         if ln == 1:
@@ -336,7 +342,8 @@ def _check_config(bbp, f, n, P, G, wide):
         if r["tail"]:
             continue
         s = F.series[r["denominator"]]
-        path, window, first = r["path"], r["window"], r["first"]
+        path, window, first, fm = r["path"], r["window"], r["first"], r["first_max"]
+        assert fm >= (1 << first) - 1
         rb = 64 if path in (1, 2) else 32
         k_last = r["k_begin"] + r["count"] - 1
         ks = sorted({r["k_begin"], min(r["k_begin"] + 1, k_last), k_last}
@@ -353,13 +360,23 @@ def _check_config(bbp, f, n, P, G, wide):
             E = d + s.c - F.step * k + W
             want = o1.term(F, s, d, k, W)
             for extra in (0, 1, 9):               # a warp tile can span E from ~64 to ~20000
-                assert ladder_term(path, window, first, m, E, W, extra, rr) % (1 << W) == want, (f, n, k, extra)
+                for take in (False, True):
+                    got = ladder_term(path, window, first, m, E, W, extra, rr, first_max=fm, take_extra=take)
+                    assert got % (1 << W) == want, (f, n, k, extra, take)
             assert ladder_term(path, window, first, m, E, W, 0, rr, valid=False) == 0
             # the largest shifts: an all-ones exponent of the same length, at the range's largest modulus
             m_max = s.a * k_last + s.b
-            E1 = rb + (1 << max(1, (E - rb).bit_length())) - 1
+            L1 = max(1, (E - rb).bit_length())
+            E1 = rb + (1 << L1) - 1
             x = ladder_term(path, window, first, m_max, E1, 64, 0, (1 << rb) % m_max)
             assert x == (-pow(2, E1, m_max) * pow(m_max, -1, 1 << 64)) % (1 << 64)
+            # the largest first window: top bits equal to first_max, then all ones
+            if fm >= 1 << first and L1 >= first + 3:
+                v2 = (fm << (L1 - first - 1)) | ((1 << (L1 - first - 1)) - 1)
+                E2 = rb + v2
+                x = ladder_term(path, window, first, m_max, E2, 64, 0, (1 << rb) % m_max, first_max=fm,
+                                take_extra=True)
+                assert x == (-pow(2, E2, m_max) * pow(m_max, -1, 1 << 64)) % (1 << 64)
             checked += 1
             paths.add(path)
     assert checked > 0

@@ -118,8 +118,9 @@ def _check_head_bounds(s, r, wide, W, d, F):
     assert 1 <= window
     # R mod m is carried from k to k + 1 with q = floor(R / m): q * a must fit 64 bits
     assert (R // m_min) * s.a < 1 << 64
-    if first:
-        w0 = (1 << first) - 1
+    fm = r["first_max"]
+    assert fm >= (1 << first) - 1 and fm < (1 << (first + 1)) - 1 or first == 4
+    for w0 in ((1 << first) - 1, fm):                                   # every first window; the largest
         assert m_max * (1 << (2 * w0 + 1)) < R                          # first squaring after the first window
         if two_limbs:
             assert m_max * (1 << w0) < 1 << 61                          # 2 x1 fits one word
