@@ -164,9 +164,10 @@ __device__ __forceinline__ void process_tile(const HeadArgs& A, const uint64_t t
     }
     const int nb = static_cast<int>(__reduce_max_sync(0xffffffffu, static_cast<uint32_t>(nbl)));
     int h = nb > 0 ? min(static_cast<int>(A.first), nb - 1) : 0;
-    if (h + 1 <= nb - 1) {
+    if (A.first_max >= (1u << h) && h + 1 <= nb - 1) {
       // one more first-window bit (one squaring fewer) when the warp's top h + 1
-      // exponent bits all stay within the first-window bound of the moduli
+      // exponent bits all stay within the first-window bound of the moduli (the
+      // lane with nb bits has top bits >= 2^h, so a smaller bound never admits it)
       uint32_t top = 0;
 #pragma unroll
       for (int t = 0; t < NT; ++t) top = max(top, static_cast<uint32_t>(v[t] >> (nb - h - 1)));
