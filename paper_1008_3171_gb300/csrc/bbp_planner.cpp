@@ -200,15 +200,12 @@ int plan_series(const FormulaDef& f, uint32_t j, uint64_t n, uint32_t W, uint32_
       }
     }
     for (const Group& g : merged) {
-      uint8_t w, h, fm;
-      window_params(g.path, g.lmax_bits, &w, &h, &fm);  // the group's largest moduli bound w0
+      // the ladder parameters of the group's largest moduli hold for all of its moduli
       TermRange r{};
+      window_params(g.path, g.lmax_bits, &r.window, &r.first, &r.first_max);
       r.j = j;
       r.tail = 0;
       r.path = static_cast<uint8_t>(g.path);
-      r.window = g.w;
-      r.first = g.h;
-      r.first_max = fm;
       r.k_begin = g.k0;
       r.count = g.k1 - g.k0;
       r.imad = range_imad(f, s, d, W, r, static_cast<int>(lmax));
