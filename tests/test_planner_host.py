@@ -148,6 +148,31 @@ def test_default_headline_plan(bbp):
     assert wide / terms > 0.999
 
 
+def test_first_window_bound_is_the_largest_the_first_squaring_allows(bbp):
+    """Every head range's first-window bound is the largest w0 with
+    bitlen(m_max) + 2 w0 + 1 <= R's width (so the extra first-window bit is not
+    given away), and its first-window width is the most bits whose every value fits
+    (at most 4): on the headline query the two-limb range of moduli up to 2^40 has
+    bound 11 over a 3-bit window, so exponents whose top four bits read 8 to 11
+    take a 4-bit first window."""
+    for f, n, P, wide in ((0, 10**12, 256, 32), (0, 10**14 + 1, 256, 32), (1, 10**9, 128, 32),
+                          (0, 10**7 + 1, 64, 5)):
+        ranges, _ = bbp.bbp_explain(f, n, P, 64, wide)
+        F = o1.FORMULAS["bellard" if f == 0 else "bbp"]
+        for r in ranges:
+            if r["tail"]:
+                continue
+            s = F.series[r["denominator"]]
+            rb = 64 if r["path"] in (1, 2) else 32
+            lmax = (s.a * (r["k_begin"] + r["count"] - 1) + s.b).bit_length()
+            assert r["first_max"] == max(0, (rb - 1 - lmax) // 2), (f, n, r)
+            h = max(i for i in range(5) if (1 << i) - 1 <= r["first_max"])
+            assert r["first"] == h, (f, n, r)
+    ranges, _ = bbp.bbp_explain(0, 10**12, 256, 64, 32)
+    top = [r for r in ranges if not r["tail"] and r["denominator"] == 2][-1]
+    assert (top["path"], top["window"], top["first"], top["first_max"]) == (1, 4, 3, 11)
+
+
 def test_crossover_moves_small_moduli_to_two_limbs(bbp):
     for wide in (5, 10, 20, 30, 32):
         ranges, _ = bbp.bbp_explain(0, 10**7 + 1, 64, 64, wide)
